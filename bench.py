@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Throughput of the fused LB-IB step on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the workload: per-object area
+and volume sums, the five membrane forces, interpolation, drag, spreading and
+node update (one kernel), then the fused D3Q19 pull-stream + BGK/Guo collide
+with bounce-back walls (one kernel).  The default workload is the
+256x128x128 channel with 200 Evans-Fung red blood cells (level-3 meshes,
+128,400 nodes), FP32 populations; the populations (628 MB) exceed the L2
+cache, so no flush is needed between steps.
+
+Printed JSON line (rank 0):
+  value        MLUPS = fluid lattice updates per second / 1e6, all ranks
+  roofline     fluid kernel: 152 B (FP32) or 76 B (FP16/BF16) per fluid cell
+               per launch / its mean CUDA-event duration, against the
+               measured copy bandwidth
+  e2e          the same metric through the public C ABI with a host loop:
+               every step uploads the per-object external forces from pinned
+               host memory, steps, and reads every object's analysis back
+  cpu_baseline the FP64 oracle on the host cores, a bounded number of full
+               steps of the same workload
+``--impl reference`` times that oracle alone on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LB+IB MLUPS & %HBM roofline, FP32 vs FP16-store; serving p50/p99 vs plain"
+BYTES_PER_CELL = {"f32": 152, "f16s": 76, "bf16s": 76}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["rbc256", "rbc512", "sphere40"], default="rbc256")
+    ap.add_argument("--precision", choices=["f32", "f16s", "bf16s"], default="f32")
+    ap.add_argument("--scale-log2", type=int, default=12, help="storage scale 2^s for f16s/bf16s")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(name):
+    from workloads import scenes
+    if name == "rbc256":
+        return scenes.channel_rbc()
+    if name == "rbc512":
+        return scenes.channel_rbc_large()
+    return scenes.channel_sphere()
+
+
+def workload_desc(sc):
+    return (f"{sc.name}: {len(sc.objects)} objects, {sc.n_nodes} nodes, "
+            f"{sc.n_fluid_cells} fluid cells, tau={sc.tau}, body force {sc.body_force[0]:g}")
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1312_3426_gb300/csrc/fluid_core.cuh", "paper_1312_3426_gb300/csrc/fluid.cu",
+                "paper_1312_3426_gb300/csrc/lbib_internal.h"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, precision, cells):
+    """DRAM bytes per launch of the fluid kernel from the committed ncu
+    summary, when it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fluid_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    rec = d.get(f"{workload}/{precision}")
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_cell"] * cells
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 8:
+                    continue
+                if self.uuid and self.uuid not in p[0] and not p[0].endswith(self.uuid):
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[4:8]))
+                except ValueError:
+                    continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(sc, target_s):
+    import oracle
+    o = oracle.Oracle.from_scene(sc)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    k = max(1, int(target_s / max(t1, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": round(sc.n_fluid_cells * k / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"{k} full FP64 steps of {sc.name} after 1 untimed step ({dt:.1f} s)",
+            "nodes_per_s": round(sc.n_nodes * k / dt, 1)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = make_scene(args.workload)
+    base = cpu_baseline(sc, min(args.cpu_seconds * 4, 120.0))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sc.n_fluid_cells / base["value"] / 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded channel, Evans-Fung RBC meshes)",
+            "config": {"workload": workload_desc(sc), "precision_storage": "f64", "parallelism": "host threads"},
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1312_3426_gb300 import build as lbuild
+    from paper_1312_3426_gb300 import lbib
+    if rank == 0:
+        lbuild.build()
+    if world > 1:
+        dist.barrier()
+    lbib.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sc = make_scene(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    sim = lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
+                              stream=stream.cuda_stream)
+    nf = sc.n_fluid_cells
+    sim.step(max(3, args.warmup))
+    sim.sync()
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    barrier()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    lbib.lbib_profile_enable(sim.h, True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    prof = lbib.lbib_profile_read(sim.h)
+    lbib.lbib_profile_enable(sim.h, False)
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * nf * args.steps / (ms / 1e3) / 1e6
+
+    fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
+    ib_ms = prof["ib_ms"] / max(1, prof["ib_launches"])
+    peak, peak_kind = measured_peak()
+    bpc = BYTES_PER_CELL[args.precision]
+    achieved = bpc * nf / (fluid_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.workload, args.precision, nf)
+
+    e2e = None
+    if not args.no_e2e:
+        nobj = len(sc.objects)
+        fh = torch.zeros((max(nobj, 1), 3), dtype=torch.float64, pin_memory=True).numpy()
+        out = torch.zeros((max(nobj, 1), 14), dtype=torch.float64, pin_memory=True).numpy()
+        k_e2e = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            if nobj:
+                lbib.lbib_objects_set_force(sim.h, fh[:nobj])
+            sim.step(1)
+            if nobj:
+                lbib.lbib_objects_analyze(sim.h, nobj, out[:nobj])
+            else:
+                sim.sync()
+        barrier()
+        dt = time.perf_counter() - t0
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(world * nf * k_e2e / float(t.item()) / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": 24 * nobj, "d2h_bytes_per_step": 14 * 8 * nobj}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(sc, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision if args.precision != "f32" else "f32",
+            "data": "synthetic (seeded channel, Evans-Fung RBC meshes at random non-overlapping poses)",
+            "config": {"workload": workload_desc(sc), "precision_storage": args.precision,
+                       "fluid_cells": nf, "nodes": sc.n_nodes, "objects": len(sc.objects),
+                       "l2": "inputs larger than L2 (populations %.0f MB), no flush" % (bpc * nf / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": f"k_fluid<{args.precision}>", "bytes_per_cell": bpc,
+                         "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
+            "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "ib": round(ib_ms, 5)},
+            "nodes_per_s": round(world * sc.n_nodes * args.steps / (ms / 1e3), 1),
+            "step_hbm_frac": round((bpc * nf + 400 * sc.n_nodes) / (ms / args.steps / 1e3) / 1e9 / peak, 4),
+            "gpu_launches": args.steps * (2 if sc.objects else 1),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": base,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * lbib.h -- C ABI of the GB300 lattice-Boltzmann / immersed-boundary step.
+ *
+ * One simulation = one D3Q19 fluid box plus elastic triangulated objects
+ * coupled to it (Cimrak, Gusenbauer, Jancigova, "An ESPResSo implementation
+ * of elastic objects immersed in a fluid", arXiv:1312.3426).  The calls
+ * follow the paper's statement of a simulation: create a template (Sec. 5,
+ * template creation), add objects from it (Sec. 5, adding of the object),
+ * initialise the fluid (Sec. 6, fluid initialisation), integrate (Sec. 6,
+ * main loop) and read out node positions, object measures and the velocity
+ * field (Sec. 5, output and object analysis).
+ *
+ * Conventions shared by every call:
+ *   - Lattice units: spacing 1, time step 1.  Lattice node (i,j,k) sits at
+ *     (i+1/2, j+1/2, k+1/2); the box is [0,nx) x [0,ny) x [0,nz).
+ *   - With walls_y = 1 the rows j = 0 and j = ny-1 are solid and the
+ *     halfway bounce-back planes are y = 1 and y = ny-1; x and z are always
+ *     periodic, y is periodic when walls_y = 0.
+ *   - All pointers are plain host pointers unless stated otherwise.  Input
+ *     arrays are owned by the caller and copied before the call returns.
+ *     Output arrays are caller-allocated; their capacity (in elements) is
+ *     passed in and LBIB_ERR_ARG is returned when it is too small.
+ *   - The library owns all device memory of a simulation; lbib_destroy
+ *     releases it.
+ *   - Every call returns a status.  lbib_last_error() gives a message for
+ *     the last failing call on that simulation.  A device-side error (a
+ *     CUDA error, an unstable fluid, a bounded device wait that gave up) is
+ *     sticky: every later call on the simulation returns it, until
+ *     lbib_destroy.
+ *   - Work is enqueued on the CUDA stream given to lbib_create (0 = legacy
+ *     default stream).  lbib_step returns before the GPU finishes; read-outs
+ *     and lbib_sync wait for it.
+ *   - The library uses the current CUDA device at lbib_create for all later
+ *     calls on that simulation.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBIB_API __attribute__((visibility("default")))
+#else
+#define LBIB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbib_sim lbib_sim;          /* opaque, library-owned */
+
+typedef enum {
+    LBIB_OK = 0,
+    LBIB_ERR_ARG = -1,       /* bad argument, capacity too small, NULL pointer */
+    LBIB_ERR_ID = -2,        /* template/object ids must run 0,1,2,... (Sec. 5) */
+    LBIB_ERR_MESH = -3,      /* not a closed, consistently inward-ordered 2-manifold */
+    LBIB_ERR_NOMEM = -4,     /* device allocation failed */
+    LBIB_ERR_UNSTABLE = -5,  /* NaN or |u| > 0.3 in the fluid, or a NaN node */
+    LBIB_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    LBIB_ERR_CUDA = -7,      /* any other CUDA error */
+    LBIB_ERR_STATE = -8      /* call out of order (e.g. step before fluid_init) */
+} lbib_status;
+
+/* Storage of the 19 populations.  All forms store h_i = f_i - w_i rho0 (the
+ * deviation from the rest equilibrium) and collide in FP32.  F16S/BF16S
+ * store h_i * 2^pop_scale_log2 rounded to nearest-even in FP16/BF16. */
+typedef enum {
+    LBIB_POP_F32 = 0,
+    LBIB_POP_F16S = 1,
+    LBIB_POP_BF16S = 2
+} lbib_precision;
+
+/* Fluid parameters (Sec. 6, fluid initialisation; Sec. 2, LB method).
+ * tau: BGK relaxation time (> 0.5; kinematic viscosity (tau - 1/2)/3).
+ * rho0: rest density.  body_force: uniform force density on every fluid
+ * cell.  friction: the drag coefficient xi of Eq. dragforce. */
+typedef struct {
+    int nx, ny, nz;
+    int walls_y;
+    double tau;
+    double rho0;
+    double body_force[3];
+    double friction;
+    int precision;           /* lbib_precision */
+    int pop_scale_log2;      /* F16S/BF16S only; 0..30 */
+} lbib_fluid_params;
+
+/* Creates a simulation: allocates the fluid on the current device (state
+ * undefined until lbib_fluid_init).  cuda_stream is a cudaStream_t or NULL.
+ * Limits: nx, nz >= 1; ny >= 3 with walls; fluid cells < 2^31. */
+LBIB_API lbib_status lbib_create(const lbib_fluid_params *params, void *cuda_stream, lbib_sim **out);
+
+/* Releases every device and host resource of the simulation. NULL is a no-op. */
+LBIB_API void lbib_destroy(lbib_sim *sim);
+
+/* Message of the last failing call (never NULL; "" when none). */
+LBIB_API const char *lbib_last_error(const lbib_sim *sim);
+
+/* Template (Sec. 5, template creation).  tid must equal the number of
+ * templates created so far.  nodes_xyz: [n_nodes][3] FP64; tris: [n_tris][3]
+ * node ids, each triangle ordered so that AB x AC points inside the object.
+ * stretch: per-axis scale of the coordinates (NULL = 1,1,1).  Moduli of
+ * Sec. 4: ks stretching, kb bending, kal local area, kag global area, kv
+ * volume; nonlinear_ks selects the neo-Hookean kappa of the stretching force
+ * (else kappa = 1).  Relaxed lengths, angles, areas, total area and volume
+ * are measured on the stretched geometry.  Errors: LBIB_ERR_ID,
+ * LBIB_ERR_MESH (open, non-manifold, inconsistent or outward-ordered),
+ * LBIB_ERR_ARG (n_nodes > 8192 or < 4). */
+LBIB_API lbib_status lbib_template_create(lbib_sim *sim, int tid, const double *nodes_xyz, int n_nodes,
+                                 const int32_t *tris, int n_tris, const double stretch[3],
+                                 double ks, double kb, double kal, double kag, double kv,
+                                 int nonlinear_ks);
+
+/* Topology and relaxed state the library built for a template.  Each output
+ * may be NULL.  edges: [ne][2] with i < j, lexicographic order.  quads:
+ * [ne][4] (a,b,c,d) for edge (b,c) = edges[e]; (a,b,c) is a cyclic order of
+ * the triangle that runs b->c and (d,c,b) of the triangle that runs c->b.
+ * L0, theta0: [ne]; S0: [n_tris]; globals: {S_g0, V0}.  *n_edges receives ne. */
+LBIB_API lbib_status lbib_template_topology(const lbib_sim *sim, int tid, int32_t *edges, int32_t *quads,
+                                   double *L0, double *theta0, double *S0, double *globals,
+                                   int *n_edges);
+
+/* Host-only mesh check (Sec. 5, mesh analysis and the template rules):
+ * validates a mesh exactly as lbib_template_create does and, when it is
+ * valid, returns the same topology and relaxed measures (outputs as for
+ * lbib_template_topology; each may be NULL; edges/quads/L0/theta0 need
+ * 3*n_tris/2 entries).  Needs no GPU.  On LBIB_ERR_MESH/LBIB_ERR_ARG the
+ * reason is written to msg (NUL-terminated, at most msg_cap bytes). */
+LBIB_API lbib_status lbib_mesh_check(const double *nodes_xyz, int n_nodes, const int32_t *tris, int n_tris,
+                                     const double stretch[3], int32_t *edges, int32_t *quads, double *L0,
+                                     double *theta0, double *S0, double *globals, int *n_edges, char *msg,
+                                     int msg_cap);
+
+/* Object (Sec. 5, adding of the object).  oid must equal the number of
+ * objects added so far.  The template geometry is rotated by rotate[0]
+ * about x, then rotate[1] about y, then rotate[2] about z (NULL = none),
+ * then translated by origin.  mass: mass of every node (> 0).  Node
+ * velocities start at 0. */
+LBIB_API lbib_status lbib_object_add(lbib_sim *sim, int oid, int tid, const double origin[3],
+                            const double rotate[3], double mass);
+
+/* External force on every node of an object (Sec. 5, object customization). */
+LBIB_API lbib_status lbib_object_set_force(lbib_sim *sim, int oid, const double f[3]);
+
+/* Replaces the node positions [n][3] of an object (Sec. 5, mesh-nodes; the
+ * restart path).  n must equal the template's node count. */
+LBIB_API lbib_status lbib_object_set_nodes(lbib_sim *sim, int oid, const double *xyz, int n);
+
+/* Replaces the node velocities [n][3] of an object. */
+LBIB_API lbib_status lbib_object_set_velocities(lbib_sim *sim, int oid, const double *v, int n);
+
+/* Fluid at rest: h_i = 0 (f_i = w_i rho0), u = 0; clears the coupling force
+ * field.  Required once before lbib_step. */
+LBIB_API lbib_status lbib_fluid_init(lbib_sim *sim);
+
+/* Advances n_steps full steps (Eq. lbequation, Eq. newton, Eq. dragforce,
+ * Sec. 4): object measures and membrane forces, interpolation, drag,
+ * spreading and node update, then fluid stream + collide with the body
+ * force plus the spread force.  Asynchronous on the simulation's stream;
+ * device-side errors surface at the next synchronising call. */
+LBIB_API lbib_status lbib_step(lbib_sim *sim, int n_steps);
+
+/* Waits for the simulation's stream and returns the sticky device status. */
+LBIB_API lbib_status lbib_sync(lbib_sim *sim);
+
+/* Node positions and/or velocities ([n][3] FP64; either may be NULL) of
+ * object oid, or of all objects in id order when oid = -1 (Sec. 5,
+ * mesh-nodes output).  cap: capacity of each array in nodes. */
+LBIB_API lbib_status lbib_read_nodes(lbib_sim *sim, int oid, double *xyz, double *v, int64_t cap);
+
+/* Fluid velocity of the last collision, [3][nz][ny][nx] FP32, 0 on solid
+ * rows (the velocity of Sec. 2 including half the applied force). */
+LBIB_API lbib_status lbib_read_velocity(lbib_sim *sim, float *u, int64_t cap);
+
+/* Fluid density [nz][ny][nx] FP32 (rho0 on solid rows). */
+LBIB_API lbib_status lbib_read_density(lbib_sim *sim, float *rho, int64_t cap);
+
+/* Populations as deviations h_i = f_i - w_i rho0, [19][nz][ny][nx] FP64 in
+ * the direction order of lbib_lattice, 0 on solid rows.  Together with
+ * lbib_set_populations this is the fluid checkpoint; for every storage
+ * precision the round trip is exact. */
+LBIB_API lbib_status lbib_read_populations(lbib_sim *sim, double *h, int64_t cap);
+LBIB_API lbib_status lbib_set_populations(lbib_sim *sim, const double *h, int64_t n);
+
+/* Object analysis (Sec. 5): out[14] = origin (mean of nodes) [3], bounds
+ * xmin,xmax,ymin,ymax,zmin,zmax [6], volume, surface area, mean node
+ * velocity [3].  Volume and area are FP64 sums on the GPU. */
+LBIB_API lbib_status lbib_object_analyze(lbib_sim *sim, int oid, double out[14]);
+
+/* Batched forms for a per-step host loop (the paper's main loop sets inputs
+ * and reads object properties every iteration, Sec. 6): set the external
+ * force of every object from f [n_obj][3] (one host-to-device copy), and
+ * analyse every object into out [n_obj][14] (one kernel, one copy back;
+ * layout as lbib_object_analyze).  cap: capacity of out in objects. */
+LBIB_API lbib_status lbib_objects_set_force(lbib_sim *sim, const double *f, int n_obj);
+LBIB_API lbib_status lbib_objects_analyze(lbib_sim *sim, double *out, int64_t cap);
+
+/* Per-phase timing with CUDA events on the simulation's stream.  While
+ * enabled, lbib_step records events around each kernel of each step.
+ * lbib_profile_read waits for the stream and returns, since the last
+ * enable: out[0] total ms and out[1] launches of the fluid kernel, out[2]
+ * total ms and out[3] launches of the object kernel. */
+LBIB_API lbib_status lbib_profile_enable(lbib_sim *sim, int on);
+LBIB_API lbib_status lbib_profile_read(lbib_sim *sim, double out[4]);
+
+/* Total fluid mass sum_cells sum_i f_i, an FP64 reduction on the GPU. */
+LBIB_API lbib_status lbib_fluid_mass(lbib_sim *sim, double *mass);
+
+/* Counts (oif_info, Sec. 5).  out[8] = n_templates, n_objects, n_nodes,
+ * fluid cells, steps taken, device bytes held, precision, reserved. */
+LBIB_API lbib_status lbib_info(const lbib_sim *sim, int64_t out[8]);
+
+/* Momentum the nodes would have given to solid corners (Sec. 2 spreading
+ * restricted to fluid nodes), summed since lbib_fluid_init. */
+LBIB_API lbib_status lbib_dropped_momentum(lbib_sim *sim, double out[3]);
+
+/* The library's D3Q19 set: e [19][3], w [19] (NULL allowed).  Returns 19. */
+LBIB_API int lbib_lattice(int32_t *e, double *w);
+
+/* Device bytes a simulation of this size would hold (fluid + coupling
+ * fields + n_nodes nodes + n_tri_total template triangles), for admission
+ * control. */
+LBIB_API int64_t lbib_footprint_bytes(const lbib_fluid_params *params, int64_t n_nodes, int64_t n_tri_total);
+
+/* Advances n simulations (same device) by n_steps each in one persistent
+ * launch per phase per step, on the stream of sims[0]; the others' streams
+ * are not used.  Each simulation's result equals that of lbib_step on it
+ * alone. */
+LBIB_API lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps);
+
+/* Version of the ABI (incremented on incompatible change). */
+LBIB_API int lbib_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIB_H */

@@ -1,0 +1,759 @@
+// C ABI of the library (declared in include/lbib.h): simulation objects,
+// templates, objects, host<->device transfers, step orchestration and the
+// sticky error model.  Host code only; the kernels live in fluid.cu, ib.cu
+// and batch.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbib.h"
+#include "lbib_internal.h"
+#include "sim.h"
+#include "topology.h"
+
+using namespace lbib;
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t pop_elem_bytes(int prec) { return prec == LBIB_POP_F32 ? 4 : 2; }
+
+struct FluidLayout {
+    int nyf, nf, nfp, nwords;
+    size_t off_pop[2], off_G[2], off_gmask[2], off_umask, off_ufield, off_status, off_dropped, total;
+};
+
+bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
+    L.nyf = p.walls_y ? p.ny - 2 : p.ny;
+    const int64_t nf = (int64_t)p.nx * L.nyf * p.nz;
+    if (nf <= 0 || nf >= (int64_t)1 << 31) return false;
+    L.nf = (int)nf;
+    L.nfp = (int)align_up((size_t)nf, 64);
+    L.nwords = (L.nf + 31) / 32;
+    size_t o = 0;
+    const size_t popb = (size_t)NQ * L.nfp * pop_elem_bytes(p.precision);
+    for (int k = 0; k < 2; ++k) { L.off_pop[k] = o; o = align_up(o + popb, 256); }
+    for (int k = 0; k < 2; ++k) { L.off_G[k] = o; o = align_up(o + (size_t)L.nf * 16, 256); }
+    for (int k = 0; k < 2; ++k) { L.off_gmask[k] = o; o = align_up(o + (size_t)L.nwords * 4, 256); }
+    L.off_umask = o; o = align_up(o + (size_t)L.nwords * 4, 256);
+    L.off_ufield = o; o = align_up(o + (size_t)L.nf * 16, 256);
+    L.off_status = o; o = align_up(o + 4, 256);
+    L.off_dropped = o; o = align_up(o + 24, 256);
+    L.total = o;
+    return true;
+}
+
+size_t template_bytes(const Topology &T) {
+    size_t o = 0;
+    o = align_up(o + (size_t)T.nt * 16, 256);
+    o = align_up(o + (size_t)(T.nn + 1) * 4, 256) * 1;
+    o = align_up(o + T.erec.size() * 4, 256);
+    o = align_up(o + (size_t)(T.nn + 1) * 4, 256);
+    o = align_up(o + T.qrec.size() * 4, 256);
+    o = align_up(o + T.qth0.size() * 4, 256);
+    o = align_up(o + (size_t)(T.nn + 1) * 4, 256);
+    o = align_up(o + T.trec.size() * 4, 256);
+    return o;
+}
+
+lbib_status fail(lbib_sim *s, lbib_status code, const std::string &msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+lbib_status cuda_fail(lbib_sim *s, cudaError_t e, const char *where) {
+    const lbib_status code = (e == cudaErrorMemoryAllocation) ? LBIB_ERR_NOMEM : LBIB_ERR_CUDA;
+    if (s) {
+        s->err = std::string(where) + ": " + cudaGetErrorString(e);
+        if (code == LBIB_ERR_CUDA) s->sticky = code;
+    }
+    return code;
+}
+
+#define LBIB_CUDA(s, call, where)                   \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail((s), e_, (where)); \
+    } while (0)
+
+#define LBIB_GUARD(s)                                                      \
+    do {                                                                   \
+        if (!(s)) return LBIB_ERR_ARG;                                     \
+        if ((s)->sticky != LBIB_OK) return (s)->sticky;                    \
+        if (cudaSetDevice((s)->device) != cudaSuccess) return LBIB_ERR_CUDA; \
+    } while (0)
+
+void rotation_zyx(const double r[3], double R[3][3]) {
+    const double cx = std::cos(r[0]), sx = std::sin(r[0]), cy = std::cos(r[1]), sy = std::sin(r[1]),
+                 cz = std::cos(r[2]), sz = std::sin(r[2]);
+    // R = Rz * Ry * Rx
+    R[0][0] = cz * cy;
+    R[0][1] = cz * sy * sx - sz * cx;
+    R[0][2] = cz * sy * cx + sz * sx;
+    R[1][0] = sz * cy;
+    R[1][1] = sz * sy * sx + cz * cx;
+    R[1][2] = sz * sy * cx - cz * sx;
+    R[2][0] = -sy;
+    R[2][1] = cy * sx;
+    R[2][2] = cy * cx;
+}
+
+}  // namespace
+
+namespace lbib {
+
+// Status word -> sticky error.
+lbib_status sim_check_status(lbib_sim *s) {
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, s->d.status, 4, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+    if (st & ST_TIMEOUT) {
+        s->sticky = LBIB_ERR_TIMEOUT;
+        s->err = "a bounded device-side wait gave up";
+    } else if (st & (ST_UNSTABLE | ST_NODE_NAN)) {
+        s->sticky = LBIB_ERR_UNSTABLE;
+        s->err = (st & ST_UNSTABLE) ? "fluid became unstable (NaN or |u| > 0.3)" : "a node position became non-finite";
+    }
+    return s->sticky;
+}
+
+lbib_status sim_download_nodes(lbib_sim *s) {
+    if (!s->dev_newer) return LBIB_OK;
+    const int nn = s->nn_total;
+    std::vector<double> X(3 * (size_t)nn), V(3 * (size_t)nn);
+    LBIB_CUDA(s, cudaMemcpyAsync(X.data(), s->dX, X.size() * 8, cudaMemcpyDeviceToHost, s->stream), "nodes D2H");
+    LBIB_CUDA(s, cudaMemcpyAsync(V.data(), s->dV, V.size() * 8, cudaMemcpyDeviceToHost, s->stream), "nodes D2H");
+    LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "nodes D2H");
+    for (int i = 0; i < nn; ++i)
+        for (int k = 0; k < 3; ++k) {
+            s->hX[3 * (size_t)i + k] = X[(size_t)k * nn + i];
+            s->hV[3 * (size_t)i + k] = V[(size_t)k * nn + i];
+        }
+    s->dev_newer = false;
+    return LBIB_OK;
+}
+
+lbib_status sim_upload(lbib_sim *s) {
+    if (s->tables_dirty) {
+        if (!s->tpl_dev.empty()) {
+            if (s->d_tpl) cudaFree(s->d_tpl);
+            s->d_tpl = nullptr;
+            LBIB_CUDA(s, cudaMalloc(&s->d_tpl, s->tpl_dev.size() * sizeof(TplDev)), "template table");
+            LBIB_CUDA(s, cudaMemcpyAsync(s->d_tpl, s->tpl_dev.data(), s->tpl_dev.size() * sizeof(TplDev),
+                                         cudaMemcpyHostToDevice, s->stream), "template table");
+        }
+        const int nobj = (int)s->objs.size();
+        if (nobj > s->d_obj_cap) {
+            const int cap = std::max(nobj, 2 * s->d_obj_cap);
+            cudaFree(s->d_obj);
+            cudaFree(s->d_fext);
+            cudaFree(s->d_analyze);
+            s->d_obj = nullptr;
+            s->d_fext = s->d_analyze = nullptr;
+            s->d_obj_cap = 0;
+            LBIB_CUDA(s, cudaMalloc(&s->d_obj, cap * sizeof(ObjDev)), "object table");
+            LBIB_CUDA(s, cudaMalloc(&s->d_fext, cap * 3 * sizeof(double)), "object forces");
+            LBIB_CUDA(s, cudaMalloc(&s->d_analyze, cap * 14 * sizeof(double)), "analysis buffer");
+            s->d_obj_cap = cap;
+            s->fext_dirty = true;
+        }
+        if (nobj > 0)
+            LBIB_CUDA(s, cudaMemcpyAsync(s->d_obj, s->objs.data(), nobj * sizeof(ObjDev), cudaMemcpyHostToDevice,
+                                         s->stream), "object table");
+        LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "tables");
+        s->d.tpl = s->d_tpl;
+        s->d.obj = s->d_obj;
+        s->d.fext = s->d_fext;
+        s->d.nobj = nobj;
+        s->tables_dirty = false;
+    }
+    if (s->fext_dirty && !s->objs.empty()) {
+        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext.data(), s->fext.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, s->stream), "object forces");
+        LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "object forces");
+        s->fext_dirty = false;
+    }
+    if (s->host_newer) {
+        const int nn = s->nn_total;
+        if (nn > s->dev_nn_cap) {
+            if (s->dX) cudaFree(s->dX);
+            if (s->dV) cudaFree(s->dV);
+            s->dX = s->dV = nullptr;
+            s->node_bytes = 0;
+            LBIB_CUDA(s, cudaMalloc(&s->dX, 3 * (size_t)nn * 8), "node state");
+            LBIB_CUDA(s, cudaMalloc(&s->dV, 3 * (size_t)nn * 8), "node state");
+            s->dev_nn_cap = nn;
+            s->node_bytes = 6 * (size_t)nn * 8;
+        }
+        std::vector<double> X(3 * (size_t)nn), V(3 * (size_t)nn);
+        for (int i = 0; i < nn; ++i)
+            for (int k = 0; k < 3; ++k) {
+                X[(size_t)k * nn + i] = s->hX[3 * (size_t)i + k];
+                V[(size_t)k * nn + i] = s->hV[3 * (size_t)i + k];
+            }
+        LBIB_CUDA(s, cudaMemcpyAsync(s->dX, X.data(), X.size() * 8, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
+        LBIB_CUDA(s, cudaMemcpyAsync(s->dV, V.data(), V.size() * 8, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
+        LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "nodes H2D");
+        s->d.X = s->dX;
+        s->d.V = s->dV;
+        s->d.nn_total = nn;
+        s->host_newer = false;
+        // the velocity samples must be valid at the (new) node corners
+        if (!(s->t == 0 && s->gmode == -1)) s->ufield_stale = true;
+    }
+    return LBIB_OK;
+}
+
+lbib_status sim_prepare_step(lbib_sim *s) {
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "lbib_fluid_init must precede lbib_step");
+    lbib_status r = sim_upload(s);
+    if (r != LBIB_OK) return r;
+    if (s->max_nodes > s->configured_nodes) {
+        LBIB_CUDA(s, ib_configure(s->max_nodes), "ib configure");
+        s->configured_nodes = s->max_nodes;
+    }
+    if (s->ufield_stale) {
+        LBIB_CUDA(s, launch_fields(s->d, (int)(s->t & 1), s->gmode, nullptr, nullptr, 1, s->stream), "velocity samples");
+        s->ufield_stale = false;
+    }
+    return LBIB_OK;
+}
+
+}  // namespace lbib
+
+extern "C" {
+
+int lbib_abi_version(void) { return 1; }
+
+int lbib_lattice(int32_t *e, double *w) {
+    for (int q = 0; q < NQ; ++q) {
+        if (e) {
+            e[3 * q] = d3q19_ex(q);
+            e[3 * q + 1] = d3q19_ey(q);
+            e[3 * q + 2] = d3q19_ez(q);
+        }
+        if (w) w[q] = d3q19_w(q);
+    }
+    return NQ;
+}
+
+int64_t lbib_footprint_bytes(const lbib_fluid_params *p, int64_t n_nodes, int64_t n_tri_total) {
+    if (!p) return -1;
+    FluidLayout L;
+    if (!fluid_layout(*p, L)) return -1;
+    // nodes: X, V (FP64); templates: ~ 3 edge + 12 bending + 3 triangle records per node
+    return (int64_t)L.total + n_nodes * 48 + n_tri_total * (16 + 3 * 16 + 4 * 20);
+}
+
+lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out) {
+    if (!p || !out) return LBIB_ERR_ARG;
+    *out = nullptr;
+    if (p->nx < 1 || p->nz < 1 || p->ny < (p->walls_y ? 3 : 1)) return LBIB_ERR_ARG;
+    if (!(p->tau > 0.5) || !(p->rho0 > 0.0) || !(p->friction >= 0.0)) return LBIB_ERR_ARG;
+    if (p->precision < 0 || p->precision > 2 || p->pop_scale_log2 < 0 || p->pop_scale_log2 > 30) return LBIB_ERR_ARG;
+    FluidLayout L;
+    if (!fluid_layout(*p, L)) return LBIB_ERR_ARG;
+    lbib_sim *s = new lbib_sim();
+    s->p = *p;
+    s->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return LBIB_ERR_CUDA;
+    }
+    cudaError_t e = cudaMalloc(&s->fluid_mem, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return e == cudaErrorMemoryAllocation ? LBIB_ERR_NOMEM : LBIB_ERR_CUDA;
+    }
+    s->fluid_bytes = L.total;
+    char *b = (char *)s->fluid_mem;
+    SimDev &d = s->d;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.walls = p->walls_y ? 1 : 0;
+    d.nyf = L.nyf;
+    d.nf = L.nf;
+    d.nfp = L.nfp;
+    d.nwords = L.nwords;
+    d.prec = p->precision;
+    d.omega = (float)(1.0 / p->tau);
+    d.fpre = (float)(1.0 - 0.5 / p->tau);
+    d.rho0 = (float)p->rho0;
+    d.gx = (float)p->body_force[0];
+    d.gy = (float)p->body_force[1];
+    d.gz = (float)p->body_force[2];
+    const int sh = p->precision == LBIB_POP_F32 ? 0 : p->pop_scale_log2;
+    d.scale = std::ldexp(1.0f, sh);
+    d.inv_scale = std::ldexp(1.0f, -sh);
+    d.xi = p->friction;
+    for (int k = 0; k < 2; ++k) {
+        d.pop[k] = b + L.off_pop[k];
+        d.G[k] = (float4 *)(b + L.off_G[k]);
+        d.gmask[k] = (uint32_t *)(b + L.off_gmask[k]);
+    }
+    d.umask = (uint32_t *)(b + L.off_umask);
+    d.ufield = (float4 *)(b + L.off_ufield);
+    d.status = (uint32_t *)(b + L.off_status);
+    d.dropped = (double *)(b + L.off_dropped);
+    e = cudaMemsetAsync(s->fluid_mem, 0, L.total, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cudaFree(s->fluid_mem);
+        delete s;
+        return LBIB_ERR_CUDA;
+    }
+    *out = s;
+    return LBIB_OK;
+}
+
+void lbib_destroy(lbib_sim *s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    for (auto &t : s->tpl_mem) cudaFree(t);
+    if (s->d_tpl) cudaFree(s->d_tpl);
+    if (s->d_obj) cudaFree(s->d_obj);
+    if (s->d_fext) cudaFree(s->d_fext);
+    if (s->d_analyze) cudaFree(s->d_analyze);
+    for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+    if (s->dX) cudaFree(s->dX);
+    if (s->dV) cudaFree(s->dV);
+    if (s->fluid_mem) cudaFree(s->fluid_mem);
+    delete s;
+}
+
+const char *lbib_last_error(const lbib_sim *s) { return s ? s->err.c_str() : "null simulation"; }
+
+lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn, const int32_t *tris, int nt,
+                                 const double stretch[3], double ks, double kb, double kal, double kag, double kv,
+                                 int nonlinear) {
+    LBIB_GUARD(s);
+    if (tid != (int)s->topo.size()) return fail(s, LBIB_ERR_ID, "template ids must be consecutive from 0");
+    if (!xyz || !tris) return fail(s, LBIB_ERR_ARG, "null mesh array");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return fail(s, LBIB_ERR_ARG, "template node count must be in [4, 8192]");
+    Topology T;
+    std::string err;
+    if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return fail(s, LBIB_ERR_MESH, err);
+    // device records, one allocation
+    const size_t bytes = template_bytes(T);
+    void *mem = nullptr;
+    LBIB_CUDA(s, cudaMalloc(&mem, bytes), "template records");
+    std::vector<char> host(bytes, 0);
+    size_t o = 0;
+    TplDev dv{};
+    auto put = [&](const void *src, size_t n) -> size_t {
+        const size_t at = o;
+        if (n) std::memcpy(host.data() + o, src, n);
+        o = align_up(o + n, 256);
+        return at;
+    };
+    std::vector<int32_t> tri4(4 * (size_t)nt, 0);
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) tri4[4 * t + k] = T.tri[3 * t + k];
+    const size_t o_tri = put(tri4.data(), tri4.size() * 4);
+    const size_t o_eoff = put(T.eoff.data(), T.eoff.size() * 4);
+    const size_t o_erec = put(T.erec.data(), T.erec.size() * 4);
+    const size_t o_qoff = put(T.qoff.data(), T.qoff.size() * 4);
+    const size_t o_qrec = put(T.qrec.data(), T.qrec.size() * 4);
+    const size_t o_qth0 = put(T.qth0.data(), T.qth0.size() * 4);
+    const size_t o_toff = put(T.toff.data(), T.toff.size() * 4);
+    const size_t o_trec = put(T.trec.data(), T.trec.size() * 4);
+    cudaError_t e = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return cuda_fail(s, e, "template H2D");
+    }
+    char *b = (char *)mem;
+    dv.nn = T.nn;
+    dv.nt = T.nt;
+    dv.ks = (float)ks;
+    dv.kb = (float)kb;
+    dv.kal = (float)kal;
+    dv.kag = (float)kag;
+    dv.kv = (float)kv;
+    dv.nonlinear = nonlinear ? 1 : 0;
+    dv.Sg0 = T.Sg0;
+    dv.V0 = T.V0;
+    dv.tri = (const int4 *)(b + o_tri);
+    dv.eoff = (const int *)(b + o_eoff);
+    dv.erec = (const int2 *)(b + o_erec);
+    dv.qoff = (const int *)(b + o_qoff);
+    dv.qrec = (const int4 *)(b + o_qrec);
+    dv.qth0 = (const float *)(b + o_qth0);
+    dv.toff = (const int *)(b + o_toff);
+    dv.trec = (const int4 *)(b + o_trec);
+    s->topo.push_back(std::move(T));
+    s->tpl_dev.push_back(dv);
+    s->tpl_mem.push_back(mem);
+    s->tpl_bytes += bytes;
+    s->max_nodes = std::max(s->max_nodes, nn);
+    s->tables_dirty = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_template_topology(const lbib_sim *s, int tid, int32_t *edges, int32_t *quads, double *L0,
+                                   double *theta0, double *S0, double *globals, int *n_edges) {
+    if (!s) return LBIB_ERR_ARG;
+    if (tid < 0 || tid >= (int)s->topo.size()) return LBIB_ERR_ID;
+    const Topology &T = s->topo[tid];
+    if (edges) std::memcpy(edges, T.edges.data(), T.edges.size() * 4);
+    if (quads) std::memcpy(quads, T.quads.data(), T.quads.size() * 4);
+    if (L0) std::memcpy(L0, T.L0.data(), T.L0.size() * 8);
+    if (theta0) std::memcpy(theta0, T.theta0.data(), T.theta0.size() * 8);
+    if (S0) std::memcpy(S0, T.S0.data(), T.S0.size() * 8);
+    if (globals) {
+        globals[0] = T.Sg0;
+        globals[1] = T.V0;
+    }
+    if (n_edges) *n_edges = T.ne;
+    return LBIB_OK;
+}
+
+lbib_status lbib_mesh_check(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
+                            int32_t *edges, int32_t *quads, double *L0, double *theta0, double *S0, double *globals,
+                            int *n_edges, char *msg, int msg_cap) {
+    auto report = [&](lbib_status code, const std::string &m) {
+        if (msg && msg_cap > 0) {
+            std::snprintf(msg, (size_t)msg_cap, "%s", m.c_str());
+        }
+        return code;
+    };
+    if (!xyz || !tris) return report(LBIB_ERR_ARG, "null mesh array");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return report(LBIB_ERR_ARG, "node count must be in [4, 8192]");
+    Topology T;
+    std::string err;
+    if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return report(LBIB_ERR_MESH, err);
+    if (edges) std::memcpy(edges, T.edges.data(), T.edges.size() * 4);
+    if (quads) std::memcpy(quads, T.quads.data(), T.quads.size() * 4);
+    if (L0) std::memcpy(L0, T.L0.data(), T.L0.size() * 8);
+    if (theta0) std::memcpy(theta0, T.theta0.data(), T.theta0.size() * 8);
+    if (S0) std::memcpy(S0, T.S0.data(), T.S0.size() * 8);
+    if (globals) {
+        globals[0] = T.Sg0;
+        globals[1] = T.V0;
+    }
+    if (n_edges) *n_edges = T.ne;
+    return report(LBIB_OK, "");
+}
+
+lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3], const double rotate[3],
+                            double mass) {
+    LBIB_GUARD(s);
+    if (oid != (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "object ids must be consecutive from 0");
+    if (tid < 0 || tid >= (int)s->topo.size()) return fail(s, LBIB_ERR_ID, "unknown template id");
+    if (!origin || !(mass > 0.0)) return fail(s, LBIB_ERR_ARG, "origin required and mass must be > 0");
+    lbib_status r = sim_download_nodes(s);
+    if (r != LBIB_OK) return r;
+    const Topology &T = s->topo[tid];
+    if ((int64_t)s->nn_total + T.nn >= ((int64_t)1 << 31)) return fail(s, LBIB_ERR_ARG, "too many nodes");
+    double R[3][3];
+    const double zero[3] = {0, 0, 0};
+    rotation_zyx(rotate ? rotate : zero, R);
+    for (int i = 0; i < T.nn; ++i) {
+        const double *x = &T.x[3 * (size_t)i];
+        for (int k = 0; k < 3; ++k) {
+            s->hX.push_back(R[k][0] * x[0] + R[k][1] * x[1] + R[k][2] * x[2] + origin[k]);
+            s->hV.push_back(0.0);
+        }
+    }
+    ObjDev ob{};
+    ob.tid = tid;
+    ob.first = s->nn_total;
+    ob.nn = T.nn;
+    ob.mass = mass;
+    s->objs.push_back(ob);
+    s->fext.insert(s->fext.end(), {0.0, 0.0, 0.0});
+    s->nn_total += T.nn;
+    s->host_newer = true;
+    s->tables_dirty = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_object_set_force(lbib_sim *s, int oid, const double f[3]) {
+    LBIB_GUARD(s);
+    if (oid < 0 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
+    if (!f) return fail(s, LBIB_ERR_ARG, "null force");
+    for (int k = 0; k < 3; ++k) s->fext[3 * (size_t)oid + k] = f[k];
+    s->fext_dirty = true;
+    return LBIB_OK;
+}
+
+static lbib_status set_node_array(lbib_sim *s, int oid, const double *src, int n, bool positions) {
+    LBIB_GUARD(s);
+    if (oid < 0 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
+    if (!src || n != s->objs[oid].nn) return fail(s, LBIB_ERR_ARG, "node count must equal the template's");
+    lbib_status r = sim_download_nodes(s);
+    if (r != LBIB_OK) return r;
+    std::vector<double> &dst = positions ? s->hX : s->hV;
+    std::memcpy(&dst[3 * (size_t)s->objs[oid].first], src, 3 * (size_t)n * 8);
+    s->host_newer = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_object_set_nodes(lbib_sim *s, int oid, const double *xyz, int n) {
+    return set_node_array(s, oid, xyz, n, true);
+}
+
+lbib_status lbib_object_set_velocities(lbib_sim *s, int oid, const double *v, int n) {
+    return set_node_array(s, oid, v, n, false);
+}
+
+lbib_status lbib_fluid_init(lbib_sim *s) {
+    LBIB_GUARD(s);
+    // everything but the sticky status word is zeroed: h = 0, G = 0, u = 0
+    FluidLayout L;
+    fluid_layout(s->p, L);
+    LBIB_CUDA(s, cudaMemsetAsync(s->fluid_mem, 0, L.off_status, s->stream), "fluid init");
+    LBIB_CUDA(s, cudaMemsetAsync((char *)s->fluid_mem + L.off_dropped, 0, 24, s->stream), "fluid init");
+    s->t = 0;
+    s->gmode = -1;
+    s->ufield_stale = false;
+    s->fluid_ready = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_step(lbib_sim *s, int n) {
+    LBIB_GUARD(s);
+    if (n < 0) return fail(s, LBIB_ERR_ARG, "negative step count");
+    lbib_status r = sim_prepare_step(s);
+    if (r != LBIB_OK) return r;
+    for (int i = 0; i < n; ++i) {
+        const int par = (int)(s->t & 1);
+        cudaEvent_t *ev = nullptr;
+        if (s->prof_on) {
+            while (s->prof_ev.size() < s->prof_used + 3) {
+                cudaEvent_t e;
+                LBIB_CUDA(s, cudaEventCreate(&e), "profile event");
+                s->prof_ev.push_back(e);
+            }
+            ev = &s->prof_ev[s->prof_used];
+            s->prof_used += 3;
+            LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
+        }
+        LBIB_CUDA(s, launch_ib(s->d, par, s->max_nodes, s->stream), "ib step");
+        if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], s->stream), "profile event");
+        LBIB_CUDA(s, launch_fluid(s->d, par, s->stream), "fluid step");
+        if (ev) LBIB_CUDA(s, cudaEventRecord(ev[2], s->stream), "profile event");
+        s->t++;
+        s->gmode = par;
+    }
+    if (n > 0 && s->nn_total > 0) s->dev_newer = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_sync(lbib_sim *s) {
+    LBIB_GUARD(s);
+    return sim_check_status(s);
+}
+
+lbib_status lbib_read_nodes(lbib_sim *s, int oid, double *xyz, double *v, int64_t cap) {
+    LBIB_GUARD(s);
+    if (oid < -1 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
+    const int64_t first = oid < 0 ? 0 : s->objs[oid].first;
+    const int64_t n = oid < 0 ? s->nn_total : s->objs[oid].nn;
+    if (cap < n) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    lbib_status r = sim_check_status(s);
+    if (r != LBIB_OK) return r;
+    r = sim_download_nodes(s);
+    if (r != LBIB_OK) return r;
+    if (xyz) std::memcpy(xyz, &s->hX[3 * first], 3 * n * 8);
+    if (v) std::memcpy(v, &s->hV[3 * first], 3 * n * 8);
+    return LBIB_OK;
+}
+
+static lbib_status read_fields(lbib_sim *s, float *u, float *rho, int64_t cap) {
+    LBIB_GUARD(s);
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (cap < (u ? 3 : 1) * ncell) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    lbib_status r = sim_check_status(s);
+    if (r != LBIB_OK) return r;
+    const size_t bytes = (size_t)(u ? 3 : 1) * ncell * 4;
+    float *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "read-out buffer");
+    cudaError_t e = cudaMemsetAsync(tmp, 0, bytes, s->stream);
+    if (e == cudaSuccess)
+        e = launch_fields(s->d, (int)(s->t & 1), s->gmode, u ? tmp : nullptr, u ? nullptr : tmp, 0, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u ? u : rho, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read-out");
+    if (rho && s->p.walls_y) {
+        for (int z = 0; z < s->p.nz; ++z)
+            for (int y : {0, s->p.ny - 1})
+                for (int x = 0; x < s->p.nx; ++x)
+                    rho[((int64_t)z * s->p.ny + y) * s->p.nx + x] = (float)s->p.rho0;
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_velocity(lbib_sim *s, float *u, int64_t cap) {
+    if (!u) return LBIB_ERR_ARG;
+    return read_fields(s, u, nullptr, cap);
+}
+
+lbib_status lbib_read_density(lbib_sim *s, float *rho, int64_t cap) {
+    if (!rho) return LBIB_ERR_ARG;
+    return read_fields(s, nullptr, rho, cap);
+}
+
+lbib_status lbib_read_populations(lbib_sim *s, double *h, int64_t cap) {
+    LBIB_GUARD(s);
+    if (!h) return fail(s, LBIB_ERR_ARG, "null output");
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (cap < NQ * ncell) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    lbib_status r = sim_check_status(s);
+    if (r != LBIB_OK) return r;
+    const size_t bytes = (size_t)NQ * ncell * 8;
+    double *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "read-out buffer");
+    cudaError_t e = cudaMemsetAsync(tmp, 0, bytes, s->stream);
+    if (e == cudaSuccess) e = launch_read_pops(s->d, (int)(s->t & 1), tmp, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read populations");
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_populations(lbib_sim *s, const double *h, int64_t n) {
+    LBIB_GUARD(s);
+    if (!h) return fail(s, LBIB_ERR_ARG, "null input");
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (n != NQ * ncell) return fail(s, LBIB_ERR_ARG, "expected 19 * nx * ny * nz values");
+    const size_t bytes = (size_t)NQ * ncell * 8;
+    double *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "upload buffer");
+    cudaError_t e = cudaMemcpyAsync(tmp, h, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = launch_set_pops(s->d, (int)(s->t & 1), tmp, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    // the coupling-force history is not part of the populations
+    FluidLayout L;
+    fluid_layout(s->p, L);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync((char *)s->fluid_mem + L.off_G[k], 0, (size_t)L.nf * 16, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync((char *)s->fluid_mem + L.off_gmask[k], 0, (size_t)L.nwords * 4, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set populations");
+    s->gmode = -2;
+    s->ufield_stale = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_object_analyze(lbib_sim *s, int oid, double out[14]) {
+    LBIB_GUARD(s);
+    if (oid < 0 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
+    if (!out) return fail(s, LBIB_ERR_ARG, "null output");
+    lbib_status r = sim_upload(s);
+    if (r != LBIB_OK) return r;
+    double *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, 14 * 8, s->stream), "analyze buffer");
+    cudaError_t e = launch_analyze(s->d, oid, tmp, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, 14 * 8, cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "analyze");
+    return LBIB_OK;
+}
+
+lbib_status lbib_fluid_mass(lbib_sim *s, double *mass) {
+    LBIB_GUARD(s);
+    if (!mass) return fail(s, LBIB_ERR_ARG, "null output");
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    double *acc = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&acc, 8, s->stream), "mass buffer");
+    cudaError_t e = cudaMemsetAsync(acc, 0, 8, s->stream);
+    double dev = 0.0;
+    if (e == cudaSuccess) e = launch_mass(s->d, (int)(s->t & 1), acc, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&dev, acc, 8, cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(acc, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "mass");
+    *mass = (double)s->d.nf * s->p.rho0 + dev;
+    return LBIB_OK;
+}
+
+lbib_status lbib_info(const lbib_sim *s, int64_t out[8]) {
+    if (!s || !out) return LBIB_ERR_ARG;
+    out[0] = (int64_t)s->topo.size();
+    out[1] = (int64_t)s->objs.size();
+    out[2] = s->nn_total;
+    out[3] = s->d.nf;
+    out[4] = s->t;
+    out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes);
+    out[6] = s->p.precision;
+    out[7] = 0;
+    return LBIB_OK;
+}
+
+lbib_status lbib_dropped_momentum(lbib_sim *s, double out[3]) {
+    LBIB_GUARD(s);
+    if (!out) return fail(s, LBIB_ERR_ARG, "null output");
+    LBIB_CUDA(s, cudaMemcpyAsync(out, s->d.dropped, 24, cudaMemcpyDeviceToHost, s->stream), "dropped");
+    LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "dropped");
+    return LBIB_OK;
+}
+
+lbib_status lbib_objects_set_force(lbib_sim *s, const double *f, int n_obj) {
+    LBIB_GUARD(s);
+    if (!f || n_obj != (int)s->objs.size()) return fail(s, LBIB_ERR_ARG, "need one force per object");
+    std::memcpy(s->fext.data(), f, 3 * (size_t)n_obj * sizeof(double));
+    s->fext_dirty = true;
+    return sim_upload(s);
+}
+
+lbib_status lbib_objects_analyze(lbib_sim *s, double *out, int64_t cap) {
+    LBIB_GUARD(s);
+    const int nobj = (int)s->objs.size();
+    if (!out || cap < nobj) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    if (nobj == 0) return LBIB_OK;
+    lbib_status r = sim_upload(s);
+    if (r != LBIB_OK) return r;
+    LBIB_CUDA(s, launch_analyze(s->d, -1, s->d_analyze, s->stream), "analyze");
+    LBIB_CUDA(s, cudaMemcpyAsync(out, s->d_analyze, (size_t)nobj * 14 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s->stream), "analyze");
+    LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "analyze");
+    return sim_check_status(s);
+}
+
+lbib_status lbib_profile_enable(lbib_sim *s, int on) {
+    LBIB_GUARD(s);
+    s->prof_on = on != 0;
+    s->prof_used = 0;
+    return LBIB_OK;
+}
+
+lbib_status lbib_profile_read(lbib_sim *s, double out[4]) {
+    LBIB_GUARD(s);
+    if (!out) return fail(s, LBIB_ERR_ARG, "null output");
+    LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "profile");
+    double fl = 0.0, ib = 0.0;
+    for (size_t k = 0; k + 3 <= s->prof_used; k += 3) {
+        float a = 0.f, b = 0.f;
+        LBIB_CUDA(s, cudaEventElapsedTime(&a, s->prof_ev[k], s->prof_ev[k + 1]), "profile");
+        LBIB_CUDA(s, cudaEventElapsedTime(&b, s->prof_ev[k + 1], s->prof_ev[k + 2]), "profile");
+        ib += a;
+        fl += b;
+    }
+    const double steps = (double)(s->prof_used / 3);
+    out[0] = fl;
+    out[1] = steps;
+    out[2] = ib;
+    out[3] = s->objs.empty() ? 0.0 : steps;
+    return LBIB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Fluid kernels: fused pull-stream + collide (Eq. lbequation), read-outs,
+// checkpoint conversion and the FP64 mass reduction.
+//
+// One thread updates one fluid cell.  For each of the 19 directions it pulls
+// the post-collision value of the previous step from the neighbour the
+// population comes from (periodic in x and z, and in y without walls); a
+// population that would come from a solid row is the cell's own opposite
+// population reflected at the halfway wall (bounce-back of a resting wall).
+// It then forms rho = rho0 + sum h, u = (sum h e + G/2)/rho with G = body
+// force + the coupling force spread onto this cell, relaxes towards the
+// equilibrium with rate 1/tau (BGK) and adds Guo's force term
+// (1 - 1/(2 tau)) w [3(e - u) + 9 (e.u) e].G.  Everything is carried as the
+// deviation h = f - w rho0 so that FP32 (or FP16/BF16 storage) keeps the
+// small velocity signal; the arithmetic is FP32.
+//
+// Memory traffic per fluid cell: 19 loads + 19 stores of the storage type
+// (152 B in FP32, 76 B in FP16/BF16), plus one 4-byte mask word per 32
+// cells for each of the three masks, plus 16 B reads/writes only at cells
+// touched by the immersed objects.
+#include "fluid_core.cuh"
+
+namespace lbib {
+
+template <typename T>
+__global__ void __launch_bounds__(FLUID_THREADS) k_fluid(SimDev s, int par) {
+    fluid_block<T>(s, par, blockIdx.x * FLUID_THREADS);
+}
+
+cudaError_t launch_fluid(const SimDev &s, int par, cudaStream_t st) {
+    const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
+    switch (s.prec) {
+        case LBIB_POP_F32: k_fluid<float><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
+        case LBIB_POP_F16S: k_fluid<__half><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
+        case LBIB_POP_BF16S: k_fluid<__nv_bfloat16><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- read-outs
+
+__device__ __forceinline__ int64_t full_index(const SimDev &s, int f) {
+    const int x = f % s.nx;
+    const int r = f / s.nx;
+    const int y = r % s.nyf + (s.walls ? 1 : 0);
+    const int z = r / s.nyf;
+    return ((int64_t)z * s.ny + y) * s.nx + x;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld_pop(const SimDev &s, int par, int q, int f) {
+    return PopIO<T>::ld((const T *)s.pop[par] + (size_t)q * s.nfp + f, s.inv_scale);
+}
+
+// Velocity and density of the last collision from the post-collision
+// populations it stored: sum f* e = sum n e + G, so u = (sum f* e - G/2)/rho.
+// gmode says which force that collision applied: -1 none (fluid as
+// initialised), -2 the body force only (populations set from the host),
+// 0 or 1 the body force plus the coupling buffer G[gmode].  The result goes
+// to full-box arrays (u [3][nz][ny][nx], rho [nz][ny][nx]) or, with
+// to_ufield, to the velocity samples of every fluid cell.
+template <typename T>
+__global__ void k_fields(SimDev s, int pop_par, int gmode, float *u, float *rho_out, int to_ufield) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= s.nf) return;
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float h = ld_pop<T>(s, pop_par, q, f);
+        drho += h;
+        jx += (float)d3q19_ex(q) * h;
+        jy += (float)d3q19_ey(q) * h;
+        jz += (float)d3q19_ez(q) * h;
+    }
+    float Gx = 0.f, Gy = 0.f, Gz = 0.f;
+    if (gmode != -1) {
+        Gx = s.gx;
+        Gy = s.gy;
+        Gz = s.gz;
+    }
+    if (gmode >= 0 && ((s.gmask[gmode][f >> 5] >> (f & 31)) & 1u)) {
+        const float4 g = s.G[gmode][f];
+        Gx += g.x;
+        Gy += g.y;
+        Gz += g.z;
+    }
+    const float rho = s.rho0 + drho;
+    const float ux = (jx - 0.5f * Gx) / rho, uy = (jy - 0.5f * Gy) / rho, uz = (jz - 0.5f * Gz) / rho;
+    if (to_ufield) {
+        s.ufield[f] = make_float4(ux, uy, uz, rho);
+        return;
+    }
+    const int64_t c = full_index(s, f);
+    const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+    if (u) {
+        u[c] = ux;
+        u[ncell + c] = uy;
+        u[2 * ncell + c] = uz;
+    }
+    if (rho_out) rho_out[c] = rho;
+}
+
+cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
+                          cudaStream_t st) {
+    const int blocks = (s.nf + 255) / 256;
+    switch (s.prec) {
+        case LBIB_POP_F32:
+            k_fields<float><<<blocks, 256, 0, st>>>(s, pop_par, gmode, u_full, rho_full, to_ufield);
+            break;
+        case LBIB_POP_F16S:
+            k_fields<__half><<<blocks, 256, 0, st>>>(s, pop_par, gmode, u_full, rho_full, to_ufield);
+            break;
+        case LBIB_POP_BF16S:
+            k_fields<__nv_bfloat16><<<blocks, 256, 0, st>>>(s, pop_par, gmode, u_full, rho_full, to_ufield);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_read_pops(SimDev s, int par, double *h) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= s.nf) return;
+    const int64_t c = full_index(s, f);
+    const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+    const T *src = (const T *)s.pop[par];
+    for (int q = 0; q < NQ; ++q) {
+        const float v = (float)PopIO<T>::ld(src + (size_t)q * s.nfp + f, 1.0f);
+        h[q * ncell + c] = (double)v * (double)s.inv_scale;
+    }
+}
+
+template <typename T>
+__global__ void k_set_pops(SimDev s, int par, const double *h) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= s.nf) return;
+    const int64_t c = full_index(s, f);
+    const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+    T *dst = (T *)s.pop[par];
+    for (int q = 0; q < NQ; ++q) {
+        const double v = h[q * ncell + c] * (double)s.scale;
+        if constexpr (sizeof(T) == 4) {
+            dst[(size_t)q * s.nfp + f] = (float)v;
+        } else {
+            PopIO<T>::st(dst + (size_t)q * s.nfp + f, (float)v, 1.0f);
+        }
+    }
+}
+
+cudaError_t launch_read_pops(const SimDev &s, int par, double *h, cudaStream_t st) {
+    const int blocks = (s.nf + 255) / 256;
+    switch (s.prec) {
+        case LBIB_POP_F32: k_read_pops<float><<<blocks, 256, 0, st>>>(s, par, h); break;
+        case LBIB_POP_F16S: k_read_pops<__half><<<blocks, 256, 0, st>>>(s, par, h); break;
+        case LBIB_POP_BF16S: k_read_pops<__nv_bfloat16><<<blocks, 256, 0, st>>>(s, par, h); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_pops(const SimDev &s, int par, const double *h, cudaStream_t st) {
+    const int blocks = (s.nf + 255) / 256;
+    switch (s.prec) {
+        case LBIB_POP_F32: k_set_pops<float><<<blocks, 256, 0, st>>>(s, par, h); break;
+        case LBIB_POP_F16S: k_set_pops<__half><<<blocks, 256, 0, st>>>(s, par, h); break;
+        case LBIB_POP_BF16S: k_set_pops<__nv_bfloat16><<<blocks, 256, 0, st>>>(s, par, h); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mass (FP64)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of all deviations h over fluid cells, FP64: each thread sums its
+// cells' 19 values in FP64, a warp shuffle and a shared-memory pass reduce
+// the block, one FP64 atomic per block adds it to *acc.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass(SimDev s, int par, double *acc) {
+    double local = 0.0;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < s.nf; f += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) local += (double)ld_pop<T>(s, par, q, f);
+    }
+    local = warp_sum(local);
+    __shared__ double part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < 8 ? part[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) atomicAdd(acc, v);
+    }
+}
+
+cudaError_t launch_mass(const SimDev &s, int par, double *acc, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int blocks = sms * 4;
+    const int need = (s.nf + 255) / 256;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    switch (s.prec) {
+        case LBIB_POP_F32: k_mass<float><<<blocks, 256, 0, st>>>(s, par, acc); break;
+        case LBIB_POP_F16S: k_mass<__half><<<blocks, 256, 0, st>>>(s, par, acc); break;
+        case LBIB_POP_BF16S: k_mass<__nv_bfloat16><<<blocks, 256, 0, st>>>(s, par, acc); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

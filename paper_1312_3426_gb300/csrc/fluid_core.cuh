@@ -1,0 +1,169 @@
+// Device-side body of the fused fluid update (Eq. lbequation), shared by the
+// single-simulation kernel (fluid.cu) and the batched persistent kernel
+// (batch.cu).  See fluid.cu for the description of the update.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbib_internal.h"
+
+namespace lbib {
+
+template <typename T>
+struct PopIO;
+
+template <>
+struct PopIO<float> {
+    static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v, float) { __stcs(p, v); }
+};
+template <>
+struct PopIO<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, float inv) { return __half2float(__ldg(p)) * inv; }
+    static __device__ __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
+};
+template <>
+struct PopIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float inv) {
+        return __bfloat162float(__ldg(p)) * inv;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sc) {
+        *p = __float2bfloat16_rn(v * sc);
+    }
+};
+
+// Neighbour offsets of one cell in the fluid index space.
+struct Nbr {
+    int dxm, dxp, dym, dyp, dzm, dzp;  // index delta to the cell at x-1, x+1, ...
+    bool ylo_solid, yhi_solid;         // the row below / above is a wall
+};
+
+__device__ __forceinline__ Nbr neighbours(const SimDev &s, int x, int y, int z) {
+    Nbr n;
+    const int plane = s.nx * s.nyf;
+    n.dxm = (x == 0) ? s.nx - 1 : -1;
+    n.dxp = (x == s.nx - 1) ? -(s.nx - 1) : 1;
+    n.dzm = (z == 0) ? (s.nz - 1) * plane : -plane;
+    n.dzp = (z == s.nz - 1) ? -(s.nz - 1) * plane : plane;
+    if (s.walls) {
+        n.ylo_solid = (y == 0);
+        n.yhi_solid = (y == s.nyf - 1);
+        n.dym = -s.nx;
+        n.dyp = s.nx;
+    } else {
+        n.ylo_solid = n.yhi_solid = false;
+        n.dym = (y == 0) ? (s.nyf - 1) * s.nx : -s.nx;
+        n.dyp = (y == s.nyf - 1) ? -(s.nyf - 1) * s.nx : s.nx;
+    }
+    return n;
+}
+
+// Pull the population of direction Q arriving at cell f.
+template <typename T, int Q>
+__device__ __forceinline__ float pull(const T *__restrict__ src, int nfp, int f, const Nbr &n, float inv) {
+    constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
+    if ((ey == 1 && n.ylo_solid) || (ey == -1 && n.yhi_solid))
+        return PopIO<T>::ld(src + (size_t)d3q19_opp(Q) * nfp + f, inv);
+    int g = f;
+    if (ex == 1) g += n.dxm;
+    if (ex == -1) g += n.dxp;
+    if (ey == 1) g += n.dym;
+    if (ey == -1) g += n.dyp;
+    if (ez == 1) g += n.dzm;
+    if (ez == -1) g += n.dzp;
+    return PopIO<T>::ld(src + (size_t)Q * nfp + g, inv);
+}
+
+template <typename T, int Q>
+__device__ __forceinline__ void collide_store(T *__restrict__ dst, int nfp, int f, float h, float drho, float rho,
+                                              float ux, float uy, float uz, float usq, float Gx, float Gy,
+                                              float Gz, float omega, float fpre, float sc) {
+    constexpr float ex = (float)d3q19_ex(Q), ey = (float)d3q19_ey(Q), ez = (float)d3q19_ez(Q);
+    constexpr float w = (float)d3q19_w(Q);
+    const float eu = ex * ux + ey * uy + ez * uz;
+    const float heq = w * (drho + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq));
+    const float eG = ex * Gx + ey * Gy + ez * Gz;
+    const float uG = ux * Gx + uy * Gy + uz * Gz;
+    const float Fq = w * (3.0f * (eG - uG) + 9.0f * eu * eG);
+    const float out = h - omega * (h - heq) + fpre * Fq;
+    PopIO<T>::st(dst + (size_t)Q * nfp + f, out, sc);
+}
+
+template <typename T>
+__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint32_t gcur, uint32_t gprv,
+                                           uint32_t um, int lane) {
+    const T *__restrict__ src = (const T *)s.pop[par];
+    T *__restrict__ dst = (T *)s.pop[par ^ 1];
+    const int nfp = s.nfp;
+    const float inv = s.inv_scale;
+    const int x = f % s.nx;
+    const int r = f / s.nx;
+    const int y = r % s.nyf;
+    const int z = r / s.nyf;
+    const Nbr n = neighbours(s, x, y, z);
+
+    float h[NQ];
+#define LBIB_PULL(q) h[q] = pull<T, q>(src, nfp, f, n, inv);
+    LBIB_PULL(0) LBIB_PULL(1) LBIB_PULL(2) LBIB_PULL(3) LBIB_PULL(4) LBIB_PULL(5) LBIB_PULL(6)
+    LBIB_PULL(7) LBIB_PULL(8) LBIB_PULL(9) LBIB_PULL(10) LBIB_PULL(11) LBIB_PULL(12) LBIB_PULL(13)
+    LBIB_PULL(14) LBIB_PULL(15) LBIB_PULL(16) LBIB_PULL(17) LBIB_PULL(18)
+#undef LBIB_PULL
+
+    const uint32_t bit = 1u << lane;
+    float Gx = s.gx, Gy = s.gy, Gz = s.gz;
+    if (gcur & bit) {
+        const float4 g = __ldcg(s.G[par] + f);
+        Gx += g.x;
+        Gy += g.y;
+        Gz += g.z;
+    }
+    if (gprv & bit) s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        drho += h[q];
+        jx += (float)d3q19_ex(q) * h[q];
+        jy += (float)d3q19_ey(q) * h[q];
+        jz += (float)d3q19_ez(q) * h[q];
+    }
+    const float rho = s.rho0 + drho;
+    const float irho = 1.0f / rho;
+    const float ux = (jx + 0.5f * Gx) * irho;
+    const float uy = (jy + 0.5f * Gy) * irho;
+    const float uz = (jz + 0.5f * Gz) * irho;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float om = s.omega, fp = s.fpre, sc = s.scale;
+#define LBIB_COLL(q) collide_store<T, q>(dst, nfp, f, h[q], drho, rho, ux, uy, uz, usq, Gx, Gy, Gz, om, fp, sc);
+    LBIB_COLL(0) LBIB_COLL(1) LBIB_COLL(2) LBIB_COLL(3) LBIB_COLL(4) LBIB_COLL(5) LBIB_COLL(6)
+    LBIB_COLL(7) LBIB_COLL(8) LBIB_COLL(9) LBIB_COLL(10) LBIB_COLL(11) LBIB_COLL(12) LBIB_COLL(13)
+    LBIB_COLL(14) LBIB_COLL(15) LBIB_COLL(16) LBIB_COLL(17) LBIB_COLL(18)
+#undef LBIB_COLL
+
+    if (um & bit) s.ufield[f] = make_float4(ux, uy, uz, rho);
+    if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
+}
+
+// One block of FLUID_THREADS consecutive fluid cells starting at f0 (a
+// multiple of 32): every warp owns the mask words of its 32 cells, consumes
+// them and clears what this step used.
+template <typename T>
+__device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0) {
+    const int f = f0 + (int)threadIdx.x;
+    const int w = f >> 5;
+    const int lane = threadIdx.x & 31;
+    uint32_t gcur = 0, gprv = 0, um = 0;
+    if (w < s.nwords) {  // L2 loads: in a batched launch other blocks set these bits
+        gcur = __ldcg(s.gmask[par] + w);
+        gprv = __ldcg(s.gmask[par ^ 1] + w);
+        um = __ldcg(s.umask + w);
+    }
+    if (f < s.nf) fluid_cell<T>(s, par, f, gcur, gprv, um, lane);
+    if (lane == 0 && w < s.nwords) {
+        if (gprv) s.gmask[par ^ 1][w] = 0u;
+        if (um) s.umask[w] = 0u;
+    }
+}
+
+}  // namespace lbib

@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of the CUDA library.
+//
+// Device data layout (one simulation):
+//   fluid cells      only the fluid rows are stored; fluid index
+//                    f = x + nx * (y' + nyf * z), y' = y - 1 with walls
+//                    (nyf = ny - 2), y' = y without (nyf = ny).
+//   populations      pop[2][19][nfp] of the storage type, direction-major
+//                    (plane stride nfp = nf rounded up to 64 elements), the
+//                    deviation h_i = f_i - w_i rho0 (times 2^s for FP16/BF16).
+//                    Step t pulls from pop[t&1] and writes pop[(t+1)&1].
+//   coupling force   G[2][nf] float4, dense but touched only where nodes
+//                    spread; bit f of gmask[2][nwords] marks a live entry.
+//                    Step t spreads into G[t&1]; the fluid step t consumes
+//                    G[t&1] and clears G[(t+1)&1] (consumed one step before),
+//                    so after step t the buffer of step t is still readable.
+//   velocity samples ufield[nf] float4 (u, rho) written by the fluid step
+//                    only at cells whose bit is set in umask: the 8 lattice
+//                    nodes around every node position, marked by the node
+//                    update of the same step and read by the next one.
+//   nodes            X[3][nn_total], V[3][nn_total] FP64, structure of
+//                    arrays, objects contiguous in id order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbib.h"
+
+namespace lbib {
+
+constexpr int NQ = 19;
+constexpr int FLUID_THREADS = 256;
+constexpr int IB_THREADS = 256;
+constexpr int MAX_TEMPLATE_NODES = 8192;
+
+// D3Q19 directions of this library: rest, the 6 axis directions in +/- pairs,
+// then the 12 face diagonals in +/- pairs; opposite(q) = q+1 for odd q,
+// q-1 for even q > 0.
+__host__ __device__ constexpr int d3q19_ex(int q) {
+    constexpr int t[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int d3q19_ey(int q) {
+    constexpr int t[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int d3q19_ez(int q) {
+    constexpr int t[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr int d3q19_opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr double d3q19_w(int q) { return q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// Device status bits (sticky per simulation).
+enum : uint32_t {
+    ST_UNSTABLE = 1u,     // NaN or |u|^2 > 0.09 in a fluid cell
+    ST_NODE_NAN = 2u,     // non-finite node position
+    ST_TIMEOUT = 4u,      // a bounded device-side wait gave up
+};
+
+// Per-node incidence records of one template (node-centric gather).
+//   erec: (neighbour id, rest length as float bits)
+//   qrec: the 4 node ids (a,b,c,d) of a bending pair, rotated so that the
+//         node owning the record is a (apex of the first triangle) or b (on
+//         the shared edge); (a,b,c) and (d,c,b) are the inward cyclic
+//         orders of the two triangles.  qth0: rest angle of that edge.
+//   trec: the triangle's ids as a cyclic rotation starting at the owner,
+//         .w = rest area as float bits.
+struct TplDev {
+    int nn, nt;
+    float ks, kb, kal, kag, kv;
+    int nonlinear;
+    double Sg0, V0;
+    const int4 *tri;      // [nt] (a, b, c, 0) as given, inward
+    const int *eoff;      // [nn+1]
+    const int2 *erec;
+    const int *qoff;      // [nn+1]
+    const int4 *qrec;
+    const float *qth0;
+    const int *toff;      // [nn+1]
+    const int4 *trec;
+};
+
+struct ObjDev {
+    int tid, first, nn, pad;
+    double mass;
+};
+
+// Everything a kernel needs to know about one simulation (POD, passed by
+// value to single-simulation kernels and stored in an array for batches).
+struct SimDev {
+    int nx, ny, nz, walls;
+    int nyf, nf, nfp, nwords;
+    int prec;                 // lbib_precision
+    float omega, fpre, rho0;  // 1/tau, 1 - 1/(2 tau), rest density
+    float gx, gy, gz;         // body force
+    float scale, inv_scale;   // 2^s, 2^-s
+    double xi;
+    void *pop[2];
+    float4 *G[2];
+    uint32_t *gmask[2];
+    uint32_t *umask;
+    float4 *ufield;
+    double *X, *V;            // [3][nn_total]
+    int nn_total, nobj;
+    const ObjDev *obj;
+    const double *fext;       // [nobj][3] external force per node of each object
+    const TplDev *tpl;
+    uint32_t *status;
+    double *dropped;          // [3]
+};
+
+// ---- launchers (fluid.cu) -------------------------------------------------
+cudaError_t launch_fluid(const SimDev &s, int par, cudaStream_t st);
+cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
+                          cudaStream_t st);
+cudaError_t launch_read_pops(const SimDev &s, int pop_par, double *h_full, cudaStream_t st);
+cudaError_t launch_set_pops(const SimDev &s, int pop_par, const double *h_full, cudaStream_t st);
+cudaError_t launch_mass(const SimDev &s, int pop_par, double *acc, cudaStream_t st);
+
+// ---- launchers (ib.cu) -----------------------------------------------------
+cudaError_t ib_configure(int max_nodes);
+cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, cudaStream_t st);
+// oid >= 0: one object into out[14]; oid < 0: every object into out[nobj][14]
+cudaError_t launch_analyze(const SimDev &s, int oid, double *out, cudaStream_t st);
+
+// ---- batched persistent step (batch.cu) -----------------------------------
+cudaError_t launch_batch_ib(const SimDev *sims_dev, const int4 *items, int n_items, int max_nodes,
+                            int par, int grid, cudaStream_t st);
+cudaError_t launch_batch_fluid(const SimDev *sims_dev, const int *sim_of_block, const int *first_block,
+                               int n_blocks, int prec, int par, int grid, unsigned *ticket, cudaStream_t st);
+
+}  // namespace lbib

@@ -1,0 +1,64 @@
+// Host-side state of one simulation (the opaque lbib_sim of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lbib.h"
+#include "lbib_internal.h"
+#include "topology.h"
+
+struct lbib_sim {
+    lbib_fluid_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    lbib_status sticky = LBIB_OK;
+
+    lbib::SimDev d{};            // device descriptor handed to kernels
+    void *fluid_mem = nullptr;   // populations, coupling fields, masks, status
+    size_t fluid_bytes = 0;
+
+    std::vector<lbib::Topology> topo;   // host copy of every template
+    std::vector<lbib::TplDev> tpl_dev;  // device descriptors of the templates
+    std::vector<void *> tpl_mem;        // device records of every template
+    size_t tpl_bytes = 0;
+    int max_nodes = 0;                  // largest template
+    int configured_nodes = 0;           // shared-memory limit set for it
+
+    std::vector<lbib::ObjDev> objs;
+    int nn_total = 0;
+    std::vector<double> hX, hV;  // host mirror of node state, [nn][3]
+    bool host_newer = false;     // host mirror changed since the last upload
+    bool dev_newer = false;      // device state advanced since the last download
+    bool tables_dirty = false;   // object/template tables need an upload
+    double *dX = nullptr, *dV = nullptr;
+    int dev_nn_cap = 0;
+    size_t node_bytes = 0;
+    lbib::ObjDev *d_obj = nullptr;
+    lbib::TplDev *d_tpl = nullptr;
+    std::vector<double> fext;    // [nobj][3]
+    double *d_fext = nullptr;
+    bool fext_dirty = false;
+    double *d_analyze = nullptr; // [nobj][14] read-out buffer
+    int d_obj_cap = 0;
+
+    bool prof_on = false;        // per-phase CUDA-event timing
+    std::vector<cudaEvent_t> prof_ev;
+    size_t prof_used = 0;
+
+    bool fluid_ready = false;
+    int64_t t = 0;               // steps since lbib_fluid_init (buffer parity)
+    int gmode = -1;              // force applied by the collision that produced the current populations
+    bool ufield_stale = false;   // velocity samples must be recomputed before the next step
+};
+
+namespace lbib {
+lbib_status sim_check_status(lbib_sim *s);
+lbib_status sim_download_nodes(lbib_sim *s);
+lbib_status sim_upload(lbib_sim *s);
+lbib_status sim_prepare_step(lbib_sim *s);
+}  // namespace lbib

@@ -1,0 +1,223 @@
+// Host-side template builder (Sec. 5, template creation; Sec. 4 relaxed
+// state).  From a triangle list it derives, by sorting directed edges:
+//   - the undirected edges (i < j) in lexicographic order,
+//   - for every edge (b,c) its bending pair (a,b,c,d): a is the third node
+//     of the triangle that runs b->c, d that of the triangle that runs c->b,
+//   - the relaxed lengths L0, inner angles theta0, triangle areas S0, total
+//     area S_g0 and volume V0 of the (stretched) template geometry, in FP64,
+//   - node-centric incidence lists used by the device gather.
+// It rejects meshes that are not closed, consistently ordered 2-manifolds,
+// meshes with unused nodes or degenerate triangles, and meshes whose
+// triangles point outward (the library requires AB x AC to point inside).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "topology.h"
+
+namespace lbib {
+
+namespace {
+
+struct V3 {
+    double x, y, z;
+};
+V3 at(const std::vector<double> &x, int i) { return {x[3 * i], x[3 * i + 1], x[3 * i + 2]}; }
+V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+double dotp(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 crossp(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double len(V3 a) { return std::sqrt(dotp(a, a)); }
+V3 unit(V3 a) {
+    const double l = len(a);
+    return {a.x / l, a.y / l, a.z / l};
+}
+
+// Inner angle at edge (b,c) between the inward-ordered triangles (a,b,c)
+// and (d,c,b): pi minus the angle between their inward normals when d lies
+// on the inner side of the first triangle's plane, pi plus it otherwise.
+double inner_angle(V3 a, V3 b, V3 c, V3 d) {
+    const V3 n1 = unit(crossp(sub(b, a), sub(c, a)));
+    const V3 n2 = unit(crossp(sub(c, d), sub(b, d)));
+    const double alpha = std::atan2(len(crossp(n1, n2)), dotp(n1, n2));
+    const double pi = 3.14159265358979323846;
+    return dotp(sub(d, b), n1) > 0.0 ? pi - alpha : pi + alpha;
+}
+
+}  // namespace
+
+bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
+                    Topology &T, std::string &err) {
+    if (nn < 4 || nt < 4) {
+        err = "a closed mesh needs at least 4 nodes and 4 triangles";
+        return false;
+    }
+    T.nn = nn;
+    T.nt = nt;
+    T.x.resize(3 * (size_t)nn);
+    for (int i = 0; i < nn; ++i)
+        for (int k = 0; k < 3; ++k) T.x[3 * i + k] = xyz[3 * i + k] * (stretch ? stretch[k] : 1.0);
+    T.tri.assign(tris, tris + 3 * (size_t)nt);
+    std::vector<int> used(nn, 0);
+    for (size_t i = 0; i < T.tri.size(); ++i) {
+        if (T.tri[i] < 0 || T.tri[i] >= nn) {
+            err = "triangle refers to a node id outside [0, n_nodes)";
+            return false;
+        }
+        used[T.tri[i]] = 1;
+    }
+    for (int t = 0; t < nt; ++t) {
+        const int a = T.tri[3 * t], b = T.tri[3 * t + 1], c = T.tri[3 * t + 2];
+        if (a == b || b == c || a == c) {
+            err = "triangle " + std::to_string(t) + " repeats a node";
+            return false;
+        }
+    }
+    for (int i = 0; i < nn; ++i)
+        if (!used[i]) {
+            err = "node " + std::to_string(i) + " belongs to no triangle";
+            return false;
+        }
+
+    // directed edges (from, to) -> apex, sorted by key
+    struct DE {
+        uint64_t key;
+        int apex;
+    };
+    std::vector<DE> de;
+    de.reserve(3 * (size_t)nt);
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t i = (uint32_t)T.tri[3 * t + k], j = (uint32_t)T.tri[3 * t + (k + 1) % 3];
+            de.push_back({((uint64_t)i << 32) | j, T.tri[3 * t + (k + 2) % 3]});
+        }
+    std::sort(de.begin(), de.end(), [](const DE &p, const DE &q) { return p.key < q.key; });
+    for (size_t k = 1; k < de.size(); ++k)
+        if (de[k].key == de[k - 1].key) {
+            err = "directed edge used twice: the mesh is non-manifold or inconsistently ordered";
+            return false;
+        }
+    auto find = [&](uint64_t key) -> int {
+        auto it = std::lower_bound(de.begin(), de.end(), key, [](const DE &p, uint64_t k) { return p.key < k; });
+        return (it != de.end() && it->key == key) ? it->apex : -1;
+    };
+    T.edges.clear();
+    T.quads.clear();
+    for (const DE &e : de) {
+        const int b = (int)(e.key >> 32), c = (int)(e.key & 0xffffffffu);
+        const int d = find(((uint64_t)(uint32_t)c << 32) | (uint32_t)b);
+        if (d < 0) {
+            err = "edge " + std::to_string(b) + "-" + std::to_string(c) + " has no opposite triangle (open mesh)";
+            return false;
+        }
+        if (b < c) {
+            T.edges.push_back(b);
+            T.edges.push_back(c);
+            T.quads.push_back(e.apex);
+            T.quads.push_back(b);
+            T.quads.push_back(c);
+            T.quads.push_back(d);
+        }
+    }
+    T.ne = (int)(T.edges.size() / 2);
+    if (2 * (size_t)T.ne != de.size()) {
+        err = "edge count inconsistent with a closed mesh";
+        return false;
+    }
+
+    // relaxed state
+    T.L0.resize(T.ne);
+    T.theta0.resize(T.ne);
+    for (int e = 0; e < T.ne; ++e) {
+        const int *q = &T.quads[4 * e];
+        T.L0[e] = len(sub(at(T.x, T.edges[2 * e + 1]), at(T.x, T.edges[2 * e])));
+        T.theta0[e] = inner_angle(at(T.x, q[0]), at(T.x, q[1]), at(T.x, q[2]), at(T.x, q[3]));
+        if (!(T.L0[e] > 0.0)) {
+            err = "zero-length edge";
+            return false;
+        }
+    }
+    T.S0.resize(nt);
+    double sg = 0.0, v6 = 0.0;
+    const V3 o = at(T.x, 0);
+    for (int t = 0; t < nt; ++t) {
+        const V3 a = sub(at(T.x, T.tri[3 * t]), o), b = sub(at(T.x, T.tri[3 * t + 1]), o),
+                 c = sub(at(T.x, T.tri[3 * t + 2]), o);
+        const double s = 0.5 * len(crossp(sub(b, a), sub(c, a)));
+        if (!(s > 0.0)) {
+            err = "degenerate triangle " + std::to_string(t);
+            return false;
+        }
+        T.S0[t] = s;
+        sg += s;
+        v6 += dotp(a, crossp(b, c));
+    }
+    T.Sg0 = sg;
+    T.V0 = -v6 / 6.0;
+    if (!(T.V0 > 0.0)) {
+        err = "triangles are ordered outward (AB x AC must point inside the object)";
+        return false;
+    }
+
+    // node-centric incidence lists
+    std::vector<int> ne(nn, 0), nq(nn, 0), ntc(nn, 0);
+    for (int e = 0; e < T.ne; ++e) {
+        ne[T.edges[2 * e]]++;
+        ne[T.edges[2 * e + 1]]++;
+        for (int k = 0; k < 4; ++k) nq[T.quads[4 * e + k]]++;
+    }
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) ntc[T.tri[3 * t + k]]++;
+    auto prefix = [nn](const std::vector<int> &cnt, std::vector<int> &off) {
+        off.assign(nn + 1, 0);
+        for (int i = 0; i < nn; ++i) off[i + 1] = off[i] + cnt[i];
+    };
+    prefix(ne, T.eoff);
+    prefix(nq, T.qoff);
+    prefix(ntc, T.toff);
+    T.erec.assign(2 * (size_t)T.eoff[nn], 0);
+    T.qrec.assign(4 * (size_t)T.qoff[nn], 0);
+    T.qth0.assign(T.qoff[nn], 0.f);
+    T.trec.assign(4 * (size_t)T.toff[nn], 0);
+    std::vector<int> fe(T.eoff.begin(), T.eoff.end() - 1), fq(T.qoff.begin(), T.qoff.end() - 1),
+        ft(T.toff.begin(), T.toff.end() - 1);
+    auto fbits = [](float f) {
+        int32_t i;
+        std::memcpy(&i, &f, sizeof(i));
+        return i;
+    };
+    for (int e = 0; e < T.ne; ++e) {
+        const int a = T.edges[2 * e], b = T.edges[2 * e + 1];
+        const int32_t l0 = fbits((float)T.L0[e]);
+        int k = fe[a]++;
+        T.erec[2 * k] = b;
+        T.erec[2 * k + 1] = l0;
+        k = fe[b]++;
+        T.erec[2 * k] = a;
+        T.erec[2 * k + 1] = l0;
+        const int *q = &T.quads[4 * e];
+        const int fwd[4] = {q[0], q[1], q[2], q[3]}, bwd[4] = {q[3], q[2], q[1], q[0]};
+        for (int r = 0; r < 4; ++r) {
+            const int owner = q[r];
+            const int *ids = (r == 0 || r == 1) ? fwd : bwd;
+            k = fq[owner]++;
+            for (int m = 0; m < 4; ++m) T.qrec[4 * k + m] = ids[m];
+            T.qth0[k] = (float)T.theta0[e];
+        }
+    }
+    for (int t = 0; t < nt; ++t) {
+        const int32_t s0 = fbits((float)T.S0[t]);
+        for (int r = 0; r < 3; ++r) {
+            const int owner = T.tri[3 * t + r];
+            const int k = ft[owner]++;
+            T.trec[4 * k] = owner;
+            T.trec[4 * k + 1] = T.tri[3 * t + (r + 1) % 3];
+            T.trec[4 * k + 2] = T.tri[3 * t + (r + 2) % 3];
+            T.trec[4 * k + 3] = s0;
+        }
+    }
+    return true;
+}
+
+}  // namespace lbib

@@ -1,0 +1,30 @@
+// Host-side template topology and relaxed state (see topology.cpp).
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace lbib {
+
+struct Topology {
+    int nn = 0, nt = 0, ne = 0;
+    std::vector<double> x;                    // stretched rest coordinates [nn][3]
+    std::vector<int> tri;                     // [nt][3] as given
+    std::vector<int> edges;                   // [ne][2], i < j, lexicographic
+    std::vector<int> quads;                   // [ne][4] (a, b, c, d)
+    std::vector<double> L0, theta0, S0;       // [ne], [ne], [nt]
+    double Sg0 = 0.0, V0 = 0.0;
+    // node-centric incidence (CSR over nodes)
+    std::vector<int> eoff, qoff, toff;        // [nn+1]
+    std::vector<int32_t> erec;                // [2 * eoff[nn]]  (neighbour, L0 bits)
+    std::vector<int32_t> qrec;                // [4 * qoff[nn]]  (a, b, c, d), owner = a or b
+    std::vector<float> qth0;                  // [qoff[nn]]
+    std::vector<int32_t> trec;                // [4 * toff[nn]]  (owner, next, next, S0 bits)
+};
+
+bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
+                    Topology &out, std::string &err);
+
+}  // namespace lbib

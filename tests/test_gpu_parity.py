@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (FP32 path): fluid velocity relative L2 over fluid cells
+<= 1e-5 and node positions max-abs <= 1e-6 lattice units after 1000 steps
+of the 40x20x20 sphere channel; the same bars on the other FP32 cases.
+FP16/BF16 storage is measured against the FP64 oracle's same-step profile
+(the FP16-shifted form must stay within 1e-3 relative L2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_3426_gb300 import lbib
+from workloads import mesh, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1312_3426_gb300 import build
+    build.build()
+    lbib.load()
+
+
+def fluid_rows(walls, ny):
+    return slice(1, ny - 1) if walls else slice(0, ny)
+
+
+def rel_l2(ug, uo, scene):
+    sl = fluid_rows(scene.walls, scene.ny)
+    a = ug[:, :, sl, :].astype(np.float64)
+    b = uo[:, :, sl, :]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def nodes_maxabs(g, o, n_obj):
+    worst = 0.0
+    for oid in range(n_obj):
+        xg, vg = g.read_nodes(oid)
+        xo, vo = o.read_nodes(oid)
+        worst = max(worst, float(np.abs(xg - xo).max()))
+    return worst
+
+
+def run_pair(scene, steps, **kw):
+    o = oracle.Oracle.from_scene(scene)
+    o.step(steps)
+    g = lbib.Sim.from_scene(scene, **kw)
+    g.step(steps)
+    g.sync()
+    return o, g
+
+
+# ------------------------------------------------------------- the 40x20x20 sphere channel
+
+def test_sphere_channel_1000_steps_matches_oracle():
+    sc = scenes.channel_sphere(steps=1000)
+    o, g = run_pair(sc, 1000)
+    err_u = rel_l2(g.velocity(), o.velocity(), sc)
+    err_x = nodes_maxabs(g, o, len(sc.objects))
+    assert err_u <= 1e-5, err_u
+    assert err_x <= 1e-6, err_x
+    # the object moved with the flow and deformed: the comparison is not trivial
+    x0 = oracle.Oracle.from_scene(sc).read_nodes(0)[0]
+    assert np.abs(o.read_nodes(0)[0] - x0).max() > 0.1
+
+
+def test_object_free_channel_matches_oracle_and_closed_form():
+    sc = scenes.channel_sphere(with_object=False)
+    o, g = run_pair(sc, 1000)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    g.step(9000)
+    u = g.velocity()[0, :, 1:-1, :].astype(np.float64)
+    nu = (sc.tau - 0.5) / 3
+    y = np.arange(1, sc.ny - 1) + 0.5
+    gx = sc.body_force[0]
+    expected = gx / (2 * nu) * (y - 1) * (sc.ny - 1 - y) + gx * (16 * (sc.tau - 0.5) ** 2 - 3) / (24 * nu)
+    err = np.abs(u - expected[None, :, None]).max() / expected.max()
+    assert err < 2e-5, err
+
+
+def test_equilibrium_stays_exact():
+    sc = scenes.channel_sphere(with_object=False)
+    sc.body_force = (0.0, 0.0, 0.0)
+    g = lbib.Sim.from_scene(sc)
+    g.step(200)
+    h = g.populations()
+    assert np.count_nonzero(h) == 0
+    assert np.count_nonzero(g.velocity()) == 0
+
+
+# ------------------------------------------------------------- ragged sizes, periodic, several objects
+
+def _two_object_scene(walls, nx=37, ny=19, nz=29, tau=0.8):
+    s = scenes.Scene("ragged", nx, ny, nz, walls=walls, tau=tau, body_force=(2e-5, 0.0, 1e-5), steps=300)
+    n2, t2 = mesh.icosphere(2)
+    r2, q2 = mesh.biconcave(2)
+    s.templates.append(scenes.Template(n2, t2, (3.0, 3.0, 3.0), ks=0.1, kb=0.03, kal=0.1, kag=0.4, kv=1.0))
+    s.templates.append(scenes.Template(r2, q2, (5.0, 5.0, 5.0), ks=0.05, kb=0.01, kal=0.0, kag=0.2, kv=10.0,
+                                       nonlinear=0))
+    s.objects.append(scenes.Obj(0, (10.3, 9.1, 8.7), (0.1, 0.2, 0.3)))
+    s.objects.append(scenes.Obj(1, (30.2, 9.6, 21.4), (1.0, -0.4, 2.2), mass=2.0, force=(1e-5, 0.0, 0.0)))
+    return s
+
+
+@pytest.mark.parametrize("walls", [True, False])
+def test_ragged_box_two_templates_matches_oracle(walls):
+    sc = _two_object_scene(walls)
+    o, g = run_pair(sc, 300)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= 1e-6
+
+
+def test_objects_crossing_the_periodic_boundary():
+    sc = _two_object_scene(True)
+    sc.objects[0].origin = (0.4, 9.1, 28.6)   # straddles x = 0 and z = nz
+    o, g = run_pair(sc, 200)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= 1e-6
+
+
+def test_node_near_wall_drops_force_like_oracle():
+    sc = _two_object_scene(True)
+    sc.objects[0].origin = (10.3, 3.2, 8.7)   # radius 3: nodes within 0.5 of the wall plane
+    o, g = run_pair(sc, 50)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= 1e-6
+    d = g.dropped()
+    assert np.abs(d).max() > 0
+    assert np.abs(d - o.dropped()).max() <= 1e-6 * np.abs(o.dropped()).max() + 1e-12
+
+
+# ------------------------------------------------------------- membrane forces alone
+
+@pytest.mark.parametrize("bit", [0, 1, 2, 3, 4])
+def test_membrane_forces_match_oracle(bit):
+    """With xi = 0 and nodes at rest, one step gives v = (F_el + F_ext)/m."""
+    nodes, tris = mesh.biconcave(3)
+    names = ["ks", "kb", "kal", "kag", "kv"]
+    k = {n: 0.0 for n in names}
+    k[names[bit]] = [0.1, 0.03, 0.1, 0.4, 1.0][bit]
+    sc = scenes.Scene("forces", 48, 48, 48, walls=False, friction=0.0, body_force=(0, 0, 0))
+    sc.templates.append(scenes.Template(nodes, tris, (8, 8, 8), **k))
+    sc.objects.append(scenes.Obj(0, (24.2, 23.9, 24.4), (0.3, 0.9, -0.2)))
+    o = oracle.Oracle.from_scene(sc)
+    g = lbib.Sim.from_scene(sc)
+    rng = np.random.default_rng(bit)
+    X, _ = o.read_nodes(0)
+    Xd = X + 0.15 * rng.standard_normal(X.shape)
+    o.object_set_nodes(0, Xd)
+    g.object_set_nodes(0, Xd)
+    F = o.membrane_forces(0, 1 << bit)
+    g.step(1)
+    _, v = g.read_nodes(0)
+    scale = np.abs(F).max()
+    assert scale > 1e-4
+    assert np.abs(v - F).max() <= 2e-5 * scale, np.abs(v - F).max() / scale
+
+
+# ------------------------------------------------------------- conservation, read-outs
+
+def test_mass_conserved_fp64_reduction():
+    sc = _two_object_scene(True)
+    g = lbib.Sim.from_scene(sc)
+    m0 = g.mass()
+    nf = sc.nx * (sc.ny - 2) * sc.nz
+    assert abs(m0 - nf) < 1e-9
+    g.step(500)
+    m1 = g.mass()
+    assert abs(m1 - m0) / m0 < 1e-9
+
+
+def test_analyze_matches_oracle():
+    sc = _two_object_scene(True)
+    o, g = run_pair(sc, 100)
+    for oid in range(2):
+        a = g.analyze(oid)
+        X, V = o.read_nodes(oid)
+        Sg, Vol = o.object_measures(oid)
+        assert np.abs(a[0:3] - X.mean(0)).max() < 1e-6
+        assert np.abs(a[3:9:2] - X.min(0)).max() < 1e-6 and np.abs(a[4:9:2] - X.max(0)).max() < 1e-6
+        assert abs(a[9] - Vol) < 1e-6 * Vol and abs(a[10] - Sg) < 1e-6 * Sg
+        assert np.abs(a[11:14] - V.mean(0)).max() < 1e-8
+
+
+def test_template_topology_equals_mesh_check():
+    sc = _two_object_scene(True)
+    g = lbib.Sim.from_scene(sc)
+    for tid, t in enumerate(sc.templates):
+        a = g.topology(tid)
+        b = lbib.lbib_mesh_check(t.nodes, t.tris, t.stretch)
+        for key in ("edges", "quads", "L0", "theta0", "S0"):
+            assert np.array_equal(a[key], b[key])
+
+
+def test_checkpoint_roundtrip_is_exact_and_restart_matches():
+    sc = _two_object_scene(True)
+    for prec, sh in (("f32", 0), ("f16s", 12), ("bf16s", 12)):
+        g = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=sh)
+        g.step(40)
+        h = g.populations()
+        X, V = g.read_nodes(-1)
+        g2 = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=sh)
+        g2.set_populations(h)
+        assert np.array_equal(g2.populations(), h)
+        g2.object_set_nodes(0, X[:162])
+        g2.object_set_velocities(0, V[:162])
+        g2.object_set_nodes(1, X[162:])
+        g2.object_set_velocities(1, V[162:])
+        g.step(20)
+        g2.step(20)
+        x1, _ = g.read_nodes(-1)
+        x2, _ = g2.read_nodes(-1)
+        assert np.abs(x1 - x2).max() < 1e-6
+        assert np.abs(g.velocity() - g2.velocity()).max() < 1e-6
+
+
+# ------------------------------------------------------------- storage precision
+
+@pytest.mark.parametrize("prec,bound", [("f16s", 1e-3), ("bf16s", 2e-2)])
+def test_shifted_half_storage_poiseuille_error(prec, bound):
+    sc = scenes.channel_sphere(with_object=False)
+    o, g = run_pair(sc, 2000, precision=prec, pop_scale_log2=12)
+    err = rel_l2(g.velocity(), o.velocity(), sc)
+    assert err <= bound, err
+    o32, g32 = run_pair(sc, 2000)
+    assert rel_l2(g32.velocity(), o32.velocity(), sc) < err
+
+
+# ------------------------------------------------------------- batching
+
+def test_batch_step_equals_individual_steps():
+    scs = [_two_object_scene(True, nx=37, ny=19, nz=29), scenes.channel_sphere(with_object=True),
+           _two_object_scene(False, nx=24, ny=20, nz=33, tau=0.9), scenes.channel_sphere(with_object=False)]
+    alone = [lbib.Sim.from_scene(s) for s in scs]
+    mixed = [lbib.Sim.from_scene(s) for s in scs]
+    for a in alone:
+        a.step(60)
+    lbib.lbib_batch_step([m.h for m in mixed], 60)
+    for s, a, m in zip(scs, alone, mixed):
+        ua, um = a.velocity(), m.velocity()
+        assert np.abs(ua - um).max() <= 1e-6 * max(1e-12, np.abs(ua).max())
+        if s.objects:
+            xa, _ = a.read_nodes(-1)
+            xm, _ = m.read_nodes(-1)
+            assert np.abs(xa - xm).max() <= 1e-9
+
+
+def test_batch_matches_oracle():
+    scs = [_two_object_scene(True), scenes.channel_sphere(with_object=True)]
+    ors = [oracle.Oracle.from_scene(s) for s in scs]
+    gs = [lbib.Sim.from_scene(s) for s in scs]
+    for o in ors:
+        o.step(200)
+    lbib.lbib_batch_step([g.h for g in gs], 200)
+    for s, o, g in zip(scs, ors, gs):
+        assert rel_l2(g.velocity(), o.velocity(), s) <= 1e-5
+        assert nodes_maxabs(g, o, len(s.objects)) <= 1e-6
+
+
+# ------------------------------------------------------------- errors (host-made, no device fault)
+
+def test_error_statuses():
+    g = lbib.Sim(16, 10, 8)
+    with pytest.raises(lbib.LbibError) as e:
+        g.step(1)
+    assert e.value.status == -8
+    nodes, tris = mesh.icosphere(1)
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.lbib_template_create(g.h, 1, nodes, tris)
+    assert e.value.status == -2
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.lbib_template_create(g.h, 0, nodes, tris[:, [0, 2, 1]])
+    assert e.value.status == -3
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.lbib_object_add(g.h, 0, 0, (1, 1, 1))
+    assert e.value.status == -2
+
+
+def test_unstable_fluid_is_reported_and_sticky():
+    g = lbib.Sim(16, 10, 8, body_force=(0.5, 0, 0))
+    g.fluid_init()
+    g.step(50)
+    with pytest.raises(lbib.LbibError) as e:
+        g.sync()
+    assert e.value.status == -5
+    with pytest.raises(lbib.LbibError) as e:
+        g.step(1)
+    assert e.value.status == -5
