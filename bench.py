@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ib-cluster", type=int, default=0, help="thread blocks per object (0: library default)")
     return ap.parse_args()
 
 
@@ -224,6 +225,8 @@ def main():
     sim = lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
                               stream=stream.cuda_stream)
     nf = sc.n_fluid_cells
+    if args.ib_cluster:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
     sim.step(max(3, args.warmup))
     sim.sync()
 

@@ -107,7 +107,7 @@ LBIB_API const char *lbib_last_error(const lbib_sim *sim);
  * (else kappa = 1).  Relaxed lengths, angles, areas, total area and volume
  * are measured on the stretched geometry.  Errors: LBIB_ERR_ID,
  * LBIB_ERR_MESH (open, non-manifold, inconsistent or outward-ordered),
- * LBIB_ERR_ARG (n_nodes > 8192 or < 4). */
+ * LBIB_ERR_ARG (n_nodes > 6144 or < 4). */
 LBIB_API lbib_status lbib_template_create(lbib_sim *sim, int tid, const double *nodes_xyz, int n_nodes,
                                  const int32_t *tris, int n_tris, const double stretch[3],
                                  double ks, double kb, double kal, double kag, double kv,
@@ -177,6 +177,16 @@ LBIB_API lbib_status lbib_read_velocity(lbib_sim *sim, float *u, int64_t cap);
 /* Fluid density [nz][ny][nx] FP32 (rho0 on solid rows). */
 LBIB_API lbib_status lbib_read_density(lbib_sim *sim, float *rho, int64_t cap);
 
+/* Force density the objects spread onto the fluid in the last step
+ * (Sec. 2, the opposite drag distributed to the grid), [3][nz][ny][nx]
+ * FP32, 0 where nothing was spread and on solid rows. */
+LBIB_API lbib_status lbib_read_coupling_force(lbib_sim *sim, float *g, int64_t cap);
+
+/* Restores the force field of lbib_read_coupling_force as the force spread
+ * in the last step (part of a checkpoint: the velocity of the last
+ * collision includes half of it).  Call after lbib_set_populations. */
+LBIB_API lbib_status lbib_set_coupling_force(lbib_sim *sim, const float *g, int64_t n);
+
 /* Populations as deviations h_i = f_i - w_i rho0, [19][nz][ny][nx] FP64 in
  * the direction order of lbib_lattice, 0 on solid rows.  Together with
  * lbib_set_populations this is the fluid checkpoint; for every storage
@@ -229,6 +239,15 @@ LBIB_API int64_t lbib_footprint_bytes(const lbib_fluid_params *params, int64_t n
  * are not used.  Each simulation's result equals that of lbib_step on it
  * alone. */
 LBIB_API lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps);
+
+/* Launch-shape knobs, chosen by the autotuner of the Python package or set
+ * by hand.  LBIB_TUNE_IB_CLUSTER: thread blocks per object in the object
+ * kernel (1..8, default 4).  Results do not depend on the knobs beyond the
+ * order of floating-point atomics.  LBIB_ERR_ARG for an unknown key or an
+ * out-of-range value. */
+typedef enum { LBIB_TUNE_IB_CLUSTER = 0 } lbib_tune_key;
+LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
+LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);
 
 /* Version of the ABI (incremented on incompatible change). */
 LBIB_API int lbib_abi_version(void);

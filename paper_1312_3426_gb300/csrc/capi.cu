@@ -50,16 +50,7 @@ bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
 }
 
 size_t template_bytes(const Topology &T) {
-    size_t o = 0;
-    o = align_up(o + (size_t)T.nt * 16, 256);
-    o = align_up(o + (size_t)(T.nn + 1) * 4, 256) * 1;
-    o = align_up(o + T.erec.size() * 4, 256);
-    o = align_up(o + (size_t)(T.nn + 1) * 4, 256);
-    o = align_up(o + T.qrec.size() * 4, 256);
-    o = align_up(o + T.qth0.size() * 4, 256);
-    o = align_up(o + (size_t)(T.nn + 1) * 4, 256);
-    o = align_up(o + T.trec.size() * 4, 256);
-    return o;
+    return align_up((size_t)T.nt * 16, 256) + 2 * align_up((size_t)T.ne * 16, 256) + align_up((size_t)T.ne * 4, 256);
 }
 
 lbib_status fail(lbib_sim *s, lbib_status code, const std::string &msg) {
@@ -127,14 +118,15 @@ lbib_status sim_check_status(lbib_sim *s) {
 lbib_status sim_download_nodes(lbib_sim *s) {
     if (!s->dev_newer) return LBIB_OK;
     const int nn = s->nn_total;
-    std::vector<double> X(3 * (size_t)nn), V(3 * (size_t)nn);
-    LBIB_CUDA(s, cudaMemcpyAsync(X.data(), s->dX, X.size() * 8, cudaMemcpyDeviceToHost, s->stream), "nodes D2H");
-    LBIB_CUDA(s, cudaMemcpyAsync(V.data(), s->dV, V.size() * 8, cudaMemcpyDeviceToHost, s->stream), "nodes D2H");
+    std::vector<float> st(12 * (size_t)nn);  // Xh, Xl, Vh, Vl, each [3][nn]
+    LBIB_CUDA(s, cudaMemcpyAsync(st.data(), s->dnodes, st.size() * 4, cudaMemcpyDeviceToHost, s->stream), "nodes D2H");
     LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "nodes D2H");
+    const size_t n3 = 3 * (size_t)nn;
     for (int i = 0; i < nn; ++i)
         for (int k = 0; k < 3; ++k) {
-            s->hX[3 * (size_t)i + k] = X[(size_t)k * nn + i];
-            s->hV[3 * (size_t)i + k] = V[(size_t)k * nn + i];
+            const size_t j = (size_t)k * nn + i;
+            s->hX[3 * (size_t)i + k] = (double)st[j] + (double)st[n3 + j];
+            s->hV[3 * (size_t)i + k] = (double)st[2 * n3 + j] + (double)st[3 * n3 + j];
         }
     s->dev_newer = false;
     return LBIB_OK;
@@ -156,10 +148,11 @@ lbib_status sim_upload(lbib_sim *s) {
             cudaFree(s->d_fext);
             cudaFree(s->d_analyze);
             s->d_obj = nullptr;
-            s->d_fext = s->d_analyze = nullptr;
+            s->d_fext = nullptr;
+            s->d_analyze = nullptr;
             s->d_obj_cap = 0;
             LBIB_CUDA(s, cudaMalloc(&s->d_obj, cap * sizeof(ObjDev)), "object table");
-            LBIB_CUDA(s, cudaMalloc(&s->d_fext, cap * 3 * sizeof(double)), "object forces");
+            LBIB_CUDA(s, cudaMalloc(&s->d_fext, cap * 3 * sizeof(float)), "object forces");
             LBIB_CUDA(s, cudaMalloc(&s->d_analyze, cap * 14 * sizeof(double)), "analysis buffer");
             s->d_obj_cap = cap;
             s->fext_dirty = true;
@@ -175,7 +168,7 @@ lbib_status sim_upload(lbib_sim *s) {
         s->tables_dirty = false;
     }
     if (s->fext_dirty && !s->objs.empty()) {
-        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext.data(), s->fext.size() * sizeof(double),
+        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext.data(), s->fext.size() * sizeof(float),
                                      cudaMemcpyHostToDevice, s->stream), "object forces");
         LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "object forces");
         s->fext_dirty = false;
@@ -183,26 +176,31 @@ lbib_status sim_upload(lbib_sim *s) {
     if (s->host_newer) {
         const int nn = s->nn_total;
         if (nn > s->dev_nn_cap) {
-            if (s->dX) cudaFree(s->dX);
-            if (s->dV) cudaFree(s->dV);
-            s->dX = s->dV = nullptr;
+            if (s->dnodes) cudaFree(s->dnodes);
+            s->dnodes = nullptr;
             s->node_bytes = 0;
-            LBIB_CUDA(s, cudaMalloc(&s->dX, 3 * (size_t)nn * 8), "node state");
-            LBIB_CUDA(s, cudaMalloc(&s->dV, 3 * (size_t)nn * 8), "node state");
+            LBIB_CUDA(s, cudaMalloc(&s->dnodes, 12 * (size_t)nn * 4), "node state");
             s->dev_nn_cap = nn;
-            s->node_bytes = 6 * (size_t)nn * 8;
+            s->node_bytes = 12 * (size_t)nn * 4;
         }
-        std::vector<double> X(3 * (size_t)nn), V(3 * (size_t)nn);
+        // FP64 host values split exactly into hi + lo FP32 pairs (48 bits)
+        std::vector<float> st(12 * (size_t)nn);
+        const size_t n3 = 3 * (size_t)nn;
         for (int i = 0; i < nn; ++i)
             for (int k = 0; k < 3; ++k) {
-                X[(size_t)k * nn + i] = s->hX[3 * (size_t)i + k];
-                V[(size_t)k * nn + i] = s->hV[3 * (size_t)i + k];
+                const size_t j = (size_t)k * nn + i;
+                const double x = s->hX[3 * (size_t)i + k], v = s->hV[3 * (size_t)i + k];
+                st[j] = (float)x;
+                st[n3 + j] = (float)(x - (double)st[j]);
+                st[2 * n3 + j] = (float)v;
+                st[3 * n3 + j] = (float)(v - (double)st[2 * n3 + j]);
             }
-        LBIB_CUDA(s, cudaMemcpyAsync(s->dX, X.data(), X.size() * 8, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
-        LBIB_CUDA(s, cudaMemcpyAsync(s->dV, V.data(), V.size() * 8, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
+        LBIB_CUDA(s, cudaMemcpyAsync(s->dnodes, st.data(), st.size() * 4, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
         LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "nodes H2D");
-        s->d.X = s->dX;
-        s->d.V = s->dV;
+        s->d.Xh = s->dnodes;
+        s->d.Xl = s->dnodes + n3;
+        s->d.Vh = s->dnodes + 2 * n3;
+        s->d.Vl = s->dnodes + 3 * n3;
         s->d.nn_total = nn;
         s->host_newer = false;
         // the velocity samples must be valid at the (new) node corners
@@ -215,10 +213,6 @@ lbib_status sim_prepare_step(lbib_sim *s) {
     if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "lbib_fluid_init must precede lbib_step");
     lbib_status r = sim_upload(s);
     if (r != LBIB_OK) return r;
-    if (s->max_nodes > s->configured_nodes) {
-        LBIB_CUDA(s, ib_configure(s->max_nodes), "ib configure");
-        s->configured_nodes = s->max_nodes;
-    }
     if (s->ufield_stale) {
         LBIB_CUDA(s, launch_fields(s->d, (int)(s->t & 1), s->gmode, nullptr, nullptr, 1, s->stream), "velocity samples");
         s->ufield_stale = false;
@@ -294,7 +288,7 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     const int sh = p->precision == LBIB_POP_F32 ? 0 : p->pop_scale_log2;
     d.scale = std::ldexp(1.0f, sh);
     d.inv_scale = std::ldexp(1.0f, -sh);
-    d.xi = p->friction;
+    d.xi = (float)p->friction;
     for (int k = 0; k < 2; ++k) {
         d.pop[k] = b + L.off_pop[k];
         d.G[k] = (float4 *)(b + L.off_G[k]);
@@ -324,9 +318,9 @@ void lbib_destroy(lbib_sim *s) {
     if (s->d_obj) cudaFree(s->d_obj);
     if (s->d_fext) cudaFree(s->d_fext);
     if (s->d_analyze) cudaFree(s->d_analyze);
+
     for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
-    if (s->dX) cudaFree(s->dX);
-    if (s->dV) cudaFree(s->dV);
+    if (s->dnodes) cudaFree(s->dnodes);
     if (s->fluid_mem) cudaFree(s->fluid_mem);
     delete s;
 }
@@ -339,7 +333,7 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     LBIB_GUARD(s);
     if (tid != (int)s->topo.size()) return fail(s, LBIB_ERR_ID, "template ids must be consecutive from 0");
     if (!xyz || !tris) return fail(s, LBIB_ERR_ARG, "null mesh array");
-    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return fail(s, LBIB_ERR_ARG, "template node count must be in [4, 8192]");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return fail(s, LBIB_ERR_ARG, "template node count must be in [4, 6144]");
     Topology T;
     std::string err;
     if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return fail(s, LBIB_ERR_MESH, err);
@@ -356,17 +350,30 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
         o = align_up(o + n, 256);
         return at;
     };
-    std::vector<int32_t> tri4(4 * (size_t)nt, 0);
-    for (int t = 0; t < nt; ++t)
+    auto fbits = [](double v) {
+        const float f = (float)v;
+        int32_t i;
+        std::memcpy(&i, &f, 4);
+        return i;
+    };
+    std::vector<int32_t> tri4(4 * (size_t)nt), edge4(4 * (size_t)T.ne), quad4(4 * (size_t)T.ne);
+    std::vector<float> ith0(T.ne);
+    for (int t = 0; t < nt; ++t) {
         for (int k = 0; k < 3; ++k) tri4[4 * t + k] = T.tri[3 * t + k];
+        tri4[4 * t + 3] = fbits(T.S0[t]);
+    }
+    for (int e = 0; e < T.ne; ++e) {
+        edge4[4 * e] = T.edges[2 * e];
+        edge4[4 * e + 1] = T.edges[2 * e + 1];
+        edge4[4 * e + 2] = fbits(T.L0[e]);
+        edge4[4 * e + 3] = fbits(1.0 / T.L0[e]);
+        for (int k = 0; k < 4; ++k) quad4[4 * e + k] = T.quads[4 * e + k];
+        ith0[e] = (float)(1.0 / T.theta0[e]);
+    }
     const size_t o_tri = put(tri4.data(), tri4.size() * 4);
-    const size_t o_eoff = put(T.eoff.data(), T.eoff.size() * 4);
-    const size_t o_erec = put(T.erec.data(), T.erec.size() * 4);
-    const size_t o_qoff = put(T.qoff.data(), T.qoff.size() * 4);
-    const size_t o_qrec = put(T.qrec.data(), T.qrec.size() * 4);
-    const size_t o_qth0 = put(T.qth0.data(), T.qth0.size() * 4);
-    const size_t o_toff = put(T.toff.data(), T.toff.size() * 4);
-    const size_t o_trec = put(T.trec.data(), T.trec.size() * 4);
+    const size_t o_edge = put(edge4.data(), edge4.size() * 4);
+    const size_t o_quad = put(quad4.data(), quad4.size() * 4);
+    const size_t o_ith0 = put(ith0.data(), ith0.size() * 4);
     cudaError_t e = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -384,14 +391,11 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     dv.nonlinear = nonlinear ? 1 : 0;
     dv.Sg0 = T.Sg0;
     dv.V0 = T.V0;
+    dv.ne = T.ne;
     dv.tri = (const int4 *)(b + o_tri);
-    dv.eoff = (const int *)(b + o_eoff);
-    dv.erec = (const int2 *)(b + o_erec);
-    dv.qoff = (const int *)(b + o_qoff);
-    dv.qrec = (const int4 *)(b + o_qrec);
-    dv.qth0 = (const float *)(b + o_qth0);
-    dv.toff = (const int *)(b + o_toff);
-    dv.trec = (const int4 *)(b + o_trec);
+    dv.edge = (const int4 *)(b + o_edge);
+    dv.quad = (const int4 *)(b + o_quad);
+    dv.inv_theta0 = (const float *)(b + o_ith0);
     s->topo.push_back(std::move(T));
     s->tpl_dev.push_back(dv);
     s->tpl_mem.push_back(mem);
@@ -429,7 +433,7 @@ lbib_status lbib_mesh_check(const double *xyz, int nn, const int32_t *tris, int 
         return code;
     };
     if (!xyz || !tris) return report(LBIB_ERR_ARG, "null mesh array");
-    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return report(LBIB_ERR_ARG, "node count must be in [4, 8192]");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return report(LBIB_ERR_ARG, "node count must be in [4, 6144]");
     Topology T;
     std::string err;
     if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return report(LBIB_ERR_MESH, err);
@@ -470,9 +474,11 @@ lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3
     ob.tid = tid;
     ob.first = s->nn_total;
     ob.nn = T.nn;
-    ob.mass = mass;
+    ob.inv_mass = (float)(1.0 / mass);
     s->objs.push_back(ob);
-    s->fext.insert(s->fext.end(), {0.0, 0.0, 0.0});
+    s->masses.push_back(mass);
+    s->fext.insert(s->fext.end(), {0.f, 0.f, 0.f});
+
     s->nn_total += T.nn;
     s->host_newer = true;
     s->tables_dirty = true;
@@ -483,7 +489,7 @@ lbib_status lbib_object_set_force(lbib_sim *s, int oid, const double f[3]) {
     LBIB_GUARD(s);
     if (oid < 0 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
     if (!f) return fail(s, LBIB_ERR_ARG, "null force");
-    for (int k = 0; k < 3; ++k) s->fext[3 * (size_t)oid + k] = f[k];
+    for (int k = 0; k < 3; ++k) s->fext[3 * (size_t)oid + k] = (float)f[k];
     s->fext_dirty = true;
     return LBIB_OK;
 }
@@ -540,9 +546,9 @@ lbib_status lbib_step(lbib_sim *s, int n) {
             s->prof_used += 3;
             LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
         }
-        LBIB_CUDA(s, launch_ib(s->d, par, s->max_nodes, s->stream), "ib step");
+        LBIB_CUDA(s, launch_ib(s->d, par, s->max_nodes, s->cluster, s->stream), "ib step");
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], s->stream), "profile event");
-        LBIB_CUDA(s, launch_fluid(s->d, par, s->stream), "fluid step");
+        LBIB_CUDA(s, launch_fluid(s->d, par, (long long)s->t, s->stream), "fluid step");
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[2], s->stream), "profile event");
         s->t++;
         s->gmode = par;
@@ -605,6 +611,49 @@ lbib_status lbib_read_velocity(lbib_sim *s, float *u, int64_t cap) {
 lbib_status lbib_read_density(lbib_sim *s, float *rho, int64_t cap) {
     if (!rho) return LBIB_ERR_ARG;
     return read_fields(s, nullptr, rho, cap);
+}
+
+lbib_status lbib_read_coupling_force(lbib_sim *s, float *g, int64_t cap) {
+    LBIB_GUARD(s);
+    if (!g) return fail(s, LBIB_ERR_ARG, "null output");
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (cap < 3 * ncell) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    lbib_status r = sim_check_status(s);
+    if (r != LBIB_OK) return r;
+    const size_t bytes = (size_t)3 * ncell * 4;
+    float *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "read-out buffer");
+    cudaError_t e = cudaMemsetAsync(tmp, 0, bytes, s->stream);
+    if (e == cudaSuccess && s->gmode >= 0) e = launch_read_coupling(s->d, s->gmode, tmp, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "read coupling force");
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_coupling_force(lbib_sim *s, const float *g, int64_t n) {
+    LBIB_GUARD(s);
+    if (!g) return fail(s, LBIB_ERR_ARG, "null input");
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (n != 3 * ncell) return fail(s, LBIB_ERR_ARG, "expected 3 * nx * ny * nz values");
+    const int gpar = (int)((s->t + 1) & 1);  // the buffer of step t - 1
+    FluidLayout L;
+    fluid_layout(s->p, L);
+    const size_t bytes = (size_t)3 * ncell * 4;
+    float *tmp = nullptr;
+    LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "upload buffer");
+    cudaError_t e = cudaMemcpyAsync(tmp, g, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync((char *)s->fluid_mem + L.off_gmask[gpar], 0, (size_t)L.nwords * 4, s->stream);
+    if (e == cudaSuccess) e = launch_set_coupling(s->d, gpar, tmp, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set coupling force");
+    s->gmode = gpar;
+    s->ufield_stale = true;
+    return LBIB_OK;
 }
 
 lbib_status lbib_read_populations(lbib_sim *s, double *h, int64_t cap) {
@@ -710,7 +759,7 @@ lbib_status lbib_dropped_momentum(lbib_sim *s, double out[3]) {
 lbib_status lbib_objects_set_force(lbib_sim *s, const double *f, int n_obj) {
     LBIB_GUARD(s);
     if (!f || n_obj != (int)s->objs.size()) return fail(s, LBIB_ERR_ARG, "need one force per object");
-    std::memcpy(s->fext.data(), f, 3 * (size_t)n_obj * sizeof(double));
+    for (size_t k = 0; k < 3 * (size_t)n_obj; ++k) s->fext[k] = (float)f[k];
     s->fext_dirty = true;
     return sim_upload(s);
 }
@@ -727,6 +776,25 @@ lbib_status lbib_objects_analyze(lbib_sim *s, double *out, int64_t cap) {
                                  s->stream), "analyze");
     LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "analyze");
     return sim_check_status(s);
+}
+
+lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
+    LBIB_GUARD(s);
+    if (key == LBIB_TUNE_IB_CLUSTER) {
+        if (value < 1 || value > 8) return fail(s, LBIB_ERR_ARG, "cluster size must be in [1, 8]");
+        s->cluster = value;
+        return LBIB_OK;
+    }
+    return fail(s, LBIB_ERR_ARG, "unknown tuning key");
+}
+
+lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
+    if (!s || !value) return LBIB_ERR_ARG;
+    if (key == LBIB_TUNE_IB_CLUSTER) {
+        *value = s->cluster;
+        return LBIB_OK;
+    }
+    return LBIB_ERR_ARG;
 }
 
 lbib_status lbib_profile_enable(lbib_sim *s, int on) {

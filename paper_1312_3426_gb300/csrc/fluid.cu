@@ -17,21 +17,24 @@
 // (152 B in FP32, 76 B in FP16/BF16), plus one 4-byte mask word per 32
 // cells for each of the three masks, plus 16 B reads/writes only at cells
 // touched by the immersed objects.
+#include <type_traits>
+
 #include "fluid_core.cuh"
 
 namespace lbib {
 
 template <typename T>
-__global__ void __launch_bounds__(FLUID_THREADS) k_fluid(SimDev s, int par) {
-    fluid_block<T>(s, par, blockIdx.x * FLUID_THREADS);
+__global__ void __launch_bounds__(FLUID_THREADS) k_fluid(SimDev s, int par, uint32_t seed) {
+    fluid_block<T>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
-cudaError_t launch_fluid(const SimDev &s, int par, cudaStream_t st) {
+cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st) {
     const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
+    const uint32_t seed = step_seed(t);
     switch (s.prec) {
-        case LBIB_POP_F32: k_fluid<float><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
-        case LBIB_POP_F16S: k_fluid<__half><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
-        case LBIB_POP_BF16S: k_fluid<__nv_bfloat16><<<blocks, FLUID_THREADS, 0, st>>>(s, par); break;
+        case LBIB_POP_F32: k_fluid<float><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
+        case LBIB_POP_F16S: k_fluid<__half><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
+        case LBIB_POP_BF16S: k_fluid<__nv_bfloat16><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -118,6 +121,39 @@ cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full
     return cudaGetLastError();
 }
 
+// Coupling force of buffer gpar (live entries only) into a full-box array.
+__global__ void k_read_coupling(SimDev s, int gpar, float *g) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= s.nf) return;
+    if (!((s.gmask[gpar][f >> 5] >> (f & 31)) & 1u)) return;
+    const float4 v = s.G[gpar][f];
+    const int64_t c = full_index(s, f);
+    const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+    g[c] = v.x;
+    g[ncell + c] = v.y;
+    g[2 * ncell + c] = v.z;
+}
+
+cudaError_t launch_read_coupling(const SimDev &s, int gpar, float *g, cudaStream_t st) {
+    k_read_coupling<<<(s.nf + 255) / 256, 256, 0, st>>>(s, gpar, g);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_coupling(SimDev s, int gpar, const float *g) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= s.nf) return;
+    const int64_t c = full_index(s, f);
+    const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+    const float4 v = make_float4(g[c], g[ncell + c], g[2 * ncell + c], 0.f);
+    s.G[gpar][f] = v;
+    if (v.x != 0.f || v.y != 0.f || v.z != 0.f) atomicOr(s.gmask[gpar] + (f >> 5), 1u << (f & 31));
+}
+
+cudaError_t launch_set_coupling(const SimDev &s, int gpar, const float *g, cudaStream_t st) {
+    k_set_coupling<<<(s.nf + 255) / 256, 256, 0, st>>>(s, gpar, g);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_read_pops(SimDev s, int par, double *h) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,7 +179,10 @@ __global__ void k_set_pops(SimDev s, int par, const double *h) {
         if constexpr (sizeof(T) == 4) {
             dst[(size_t)q * s.nfp + f] = (float)v;
         } else {
-            PopIO<T>::st(dst + (size_t)q * s.nfp + f, (float)v, 1.0f);
+            if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value)
+                dst[(size_t)q * s.nfp + f] = __float2half_rn((float)v);
+            else
+                dst[(size_t)q * s.nfp + f] = __float2bfloat16_rn((float)v);
         }
     }
 }

@@ -10,28 +10,50 @@
 
 namespace lbib {
 
+// Storage of one population.  FP32 is stored as is.  FP16/BF16 store the
+// deviation times 2^s with stochastic rounding: a random integer below the
+// weight of the first dropped bit is added to the FP32 bit pattern, which is
+// then truncated, so the stored value is unbiased.  Rounding to nearest
+// would turn the per-step forcing increment, which is far below one unit in
+// the last place of a 16-bit number once the flow has built up, into a
+// systematic error.  The random bits come from a counter-based hash of
+// (cell, step, direction), so results are reproducible.
 template <typename T>
 struct PopIO;
 
 template <>
 struct PopIO<float> {
     static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float v, float) { __stcs(p, v); }
+    static __device__ __forceinline__ void st(float *p, float v, float, uint32_t) { __stcs(p, v); }
 };
 template <>
 struct PopIO<__half> {
     static __device__ __forceinline__ float ld(const __half *p, float inv) { return __half2float(__ldg(p)) * inv; }
-    static __device__ __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
+    static __device__ __forceinline__ void st(__half *p, float v, float sc, uint32_t rnd) {
+        const uint32_t b = __float_as_uint(v * sc) + (rnd & 0x1fffu);  // 13 bits dropped by FP16
+        *p = __float2half_rz(__uint_as_float(b));
+    }
 };
 template <>
 struct PopIO<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float inv) {
         return __bfloat162float(__ldg(p)) * inv;
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sc) {
-        *p = __float2bfloat16_rn(v * sc);
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sc, uint32_t rnd) {
+        const uint32_t b = __float_as_uint(v * sc) + (rnd & 0xffffu);  // 16 bits dropped by BF16
+        *p = __float2bfloat16_rz(__uint_as_float(b));
     }
 };
+
+// 32-bit integer hash (xor-shift / multiply finaliser) for the rounding bits.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 // Neighbour offsets of one cell in the fluid index space.
 struct Nbr {
@@ -78,7 +100,7 @@ __device__ __forceinline__ float pull(const T *__restrict__ src, int nfp, int f,
 template <typename T, int Q>
 __device__ __forceinline__ void collide_store(T *__restrict__ dst, int nfp, int f, float h, float drho, float rho,
                                               float ux, float uy, float uz, float usq, float Gx, float Gy,
-                                              float Gz, float omega, float fpre, float sc) {
+                                              float Gz, float omega, float fpre, float sc, uint32_t &rng) {
     constexpr float ex = (float)d3q19_ex(Q), ey = (float)d3q19_ey(Q), ez = (float)d3q19_ez(Q);
     constexpr float w = (float)d3q19_w(Q);
     const float eu = ex * ux + ey * uy + ez * uz;
@@ -87,12 +109,17 @@ __device__ __forceinline__ void collide_store(T *__restrict__ dst, int nfp, int 
     const float uG = ux * Gx + uy * Gy + uz * Gz;
     const float Fq = w * (3.0f * (eG - uG) + 9.0f * eu * eG);
     const float out = h - omega * (h - heq) + fpre * Fq;
-    PopIO<T>::st(dst + (size_t)Q * nfp + f, out, sc);
+    uint32_t rnd = 0;
+    if (sizeof(T) == 2) {  // one linear-congruential step per population
+        rng = rng * 747796405u + 2891336453u;
+        rnd = rng ^ (rng >> 15);
+    }
+    PopIO<T>::st(dst + (size_t)Q * nfp + f, out, sc, rnd);
 }
 
 template <typename T>
 __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint32_t gcur, uint32_t gprv,
-                                           uint32_t um, int lane) {
+                                           uint32_t um, int lane, uint32_t step_seed) {
     const T *__restrict__ src = (const T *)s.pop[par];
     T *__restrict__ dst = (T *)s.pop[par ^ 1];
     const int nfp = s.nfp;
@@ -135,7 +162,8 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint
     const float uz = (jz + 0.5f * Gz) * irho;
     const float usq = ux * ux + uy * uy + uz * uz;
     const float om = s.omega, fp = s.fpre, sc = s.scale;
-#define LBIB_COLL(q) collide_store<T, q>(dst, nfp, f, h[q], drho, rho, ux, uy, uz, usq, Gx, Gy, Gz, om, fp, sc);
+    uint32_t rng = (sizeof(T) == 2) ? mix32((uint32_t)f ^ step_seed) : 0u;
+#define LBIB_COLL(q) collide_store<T, q>(dst, nfp, f, h[q], drho, rho, ux, uy, uz, usq, Gx, Gy, Gz, om, fp, sc, rng);
     LBIB_COLL(0) LBIB_COLL(1) LBIB_COLL(2) LBIB_COLL(3) LBIB_COLL(4) LBIB_COLL(5) LBIB_COLL(6)
     LBIB_COLL(7) LBIB_COLL(8) LBIB_COLL(9) LBIB_COLL(10) LBIB_COLL(11) LBIB_COLL(12) LBIB_COLL(13)
     LBIB_COLL(14) LBIB_COLL(15) LBIB_COLL(16) LBIB_COLL(17) LBIB_COLL(18)
@@ -145,11 +173,20 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint
     if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
 }
 
+// Seed of the rounding bits of step t.
+__host__ __device__ __forceinline__ uint32_t step_seed(long long t) {
+    uint32_t x = (uint32_t)t * 0x9e3779b9u + 0x632be5abu;
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    return x;
+}
+
 // One block of FLUID_THREADS consecutive fluid cells starting at f0 (a
 // multiple of 32): every warp owns the mask words of its 32 cells, consumes
 // them and clears what this step used.
 template <typename T>
-__device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0) {
+__device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0, uint32_t step_seed) {
     const int f = f0 + (int)threadIdx.x;
     const int w = f >> 5;
     const int lane = threadIdx.x & 31;
@@ -159,7 +196,7 @@ __device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0) {
         gprv = __ldcg(s.gmask[par ^ 1] + w);
         um = __ldcg(s.umask + w);
     }
-    if (f < s.nf) fluid_cell<T>(s, par, f, gcur, gprv, um, lane);
+    if (f < s.nf) fluid_cell<T>(s, par, f, gcur, gprv, um, lane, step_seed);
     if (lane == 0 && w < s.nwords) {
         if (gprv) s.gmask[par ^ 1][w] = 0u;
         if (um) s.umask[w] = 0u;

@@ -1,7 +1,44 @@
-// Device-side body of the per-object immersed-boundary update, shared by the
-// single-simulation kernel (ib.cu) and the batched persistent kernel
-// (batch.cu).  See ib.cu for the description of the update.
+// Device-side body of the immersed-boundary update (Sec. 2 and Sec. 4 of
+// arXiv:1312.3426), shared by the single-simulation kernel (ib.cu) and the
+// batched persistent kernel (batch.cu).
+//
+// One thread-block cluster of C blocks updates one object:
+//   1. every block stages the positions of all the object's nodes, relative
+//      to its first node, as hi + lo FP32 pairs in shared memory, and clears
+//      its own force array;
+//   2. every block sums the area and divergence-theorem volume terms of its
+//      share of the triangles (error-free FP32 pair sums); after a cluster
+//      barrier one thread per block reads the C partial sums through
+//      distributed shared memory in a fixed order and forms the object's
+//      total area S_g and volume V in FP64 (Sec. 4, global area and volume
+//      conservation);
+//   3. every block evaluates its share of the elements and adds each
+//      contribution to its own shared-memory force array:
+//        edge       stretching (Eq. stretching) ks kappa(lambda) (L-L0)/L0
+//                   along the edge, +f on one node, -f on the other;
+//        edge pair  bending: theta is the inner angle between the triangles
+//                   (a,b,c) and (d,c,b), s = kb (theta-theta0)/theta0, the
+//                   apices take s n1 and s n2 (inward unit normals), the edge
+//                   nodes minus half of their sum;
+//        triangle   local area -kal (S-S0)/S w_v and global area
+//                   -kag (S_g-S_g0)/S_g w_v, w_v the unit vector from the
+//                   centroid to vertex v, and volume kv (V-V0)/V0 S n_in / 3;
+//      a pair of opposite contributions is the same FP32 value with both
+//      signs, so internal forces cancel up to the rounding of the sums;
+//   4. after a cluster barrier every block takes its share of the nodes, sums
+//      the C partial force arrays through distributed shared memory in a
+//      fixed order, interpolates the fluid velocity trilinearly from the 8
+//      surrounding lattice nodes (u = 0 on solid rows), applies the drag
+//      F_d = xi (u - v), spreads -F_d with the same weights (one 16-byte
+//      vector atomic per corner plus a bit in the live-entry mask) and
+//      advances v += (F + F_d + F_ext)/m, X += v (Eq. newton, unit time
+//      step); the 8 lattice nodes around the new position are marked so that
+//      the next fluid step writes their velocity.
+// Node state is kept as hi + lo FP32 pairs (error-free two-sum arithmetic);
+// FP64 is used only for the per-object area and volume totals.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "lbib_internal.h"
 
@@ -18,10 +55,40 @@ __device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y 
 __device__ __forceinline__ f3 cross(f3 a, f3 b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
+__device__ __forceinline__ f3 xyz(float4 v) { return {v.x, v.y, v.z}; }
+__device__ __forceinline__ float4 f4(f3 v, float w) { return make_float4(v.x, v.y, v.z, w); }
 
+// Error-free FP32 transformations (Knuth's two-sum and its fast variant):
+// a pair (hi, lo) holds the unevaluated sum hi + lo.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+
+// Staged positions of one object: node q relative to the object's first
+// node is (hx[q] + lx[q], hy[q] + ly[q], hz[q] + lz[q]).
 struct Stage {
     const float *hx, *hy, *hz, *lx, *ly, *lz;
-    // position of node q relative to node p
+    // position of node q relative to node p; the difference of the hi parts
+    // is exact for the nearby nodes of one element
     __device__ __forceinline__ f3 rel(int q, int p) const {
         return {(hx[q] - hx[p]) + (lx[q] - lx[p]), (hy[q] - hy[p]) + (ly[q] - ly[p]),
                 (hz[q] - hz[p]) + (lz[q] - lz[p])};
@@ -57,13 +124,32 @@ struct Corners {
     float w[8];
 };
 
+// Lower lattice index and fraction of one coordinate given as hi + lo:
+// i0 = floor(x - 1/2), w = x - 1/2 - i0 in [0, 1).  x.hi - 1/2 and the
+// subtraction of the integer are exact for |x| < 2^22.
+__device__ __forceinline__ void lattice_coord(df x, int &i0, float &w) {
+    const float p = x.hi - 0.5f;
+    float fl = floorf(p);
+    float fr = (p - fl) + x.lo;
+    if (fr < 0.f) {
+        fl -= 1.f;
+        fr += 1.f;
+    } else if (fr >= 1.f) {
+        fl += 1.f;
+        fr -= 1.f;
+    }
+    i0 = (int)fl;
+    w = fr;
+}
+
 // Trilinear weights: corner (i0+dx, j0+dy, k0+dz) gets the volume of the
 // box between the point and the diagonally opposite corner.
-__device__ __forceinline__ void corners(const SimDev &s, double x, double y, double z, Corners &c) {
-    const double px = x - 0.5, py = y - 0.5, pz = z - 0.5;
-    const double fx = floor(px), fy = floor(py), fz = floor(pz);
-    const float wx = (float)(px - fx), wy = (float)(py - fy), wz = (float)(pz - fz);
-    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+__device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corners &c) {
+    int ix, iy, iz;
+    float wx, wy, wz;
+    lattice_coord(x, ix, wx);
+    lattice_coord(y, iy, wy);
+    lattice_coord(z, iz, wz);
     const int cx0 = wrapi(ix, s.nx), cx1 = wrapi(ix + 1, s.nx);
     const int cz0 = wrapi(iz, s.nz), cz1 = wrapi(iz + 1, s.nz);
 #pragma unroll
@@ -76,180 +162,262 @@ __device__ __forceinline__ void corners(const SimDev &s, double x, double y, dou
 
 __device__ __forceinline__ void mark(uint32_t *mask, int f) { atomicOr(mask + (f >> 5), 1u << (f & 31)); }
 
-// Shared memory: 6 floats per node of the largest template.
-constexpr int IB_SMEM_PER_NODE = 6 * sizeof(float);
+namespace cg = cooperative_groups;
 
-__device__ __forceinline__ void ib_object(const SimDev &s, int o, int par, float *sh) {
-    __syncthreads();  // a persistent block may still read the previous object's staging
-    const ObjDev ob = s.obj[o];
-    const TplDev T = s.tpl[ob.tid];
-    const int nn = ob.nn;
-    const int NN = s.nn_total;
-    double *Xx = s.X, *Xy = s.X + NN, *Xz = s.X + 2 * NN;
-    double *Vx = s.V, *Vy = s.V + NN, *Vz = s.V + 2 * NN;
+// Shared memory per block: 9 floats per node of the largest template (staged
+// position hi/lo, force) plus a small fixed tail.
+constexpr int IB_SMEM_PER_NODE = 9 * sizeof(float);
+constexpr int IB_SMEM_TAIL = 64;
 
-    Stage P{sh, sh + nn, sh + 2 * nn, sh + 3 * nn, sh + 4 * nn, sh + 5 * nn};
-    const double Rx = Xx[ob.first], Ry = Xy[ob.first], Rz = Xz[ob.first];
-    for (int p = threadIdx.x; p < nn; p += IB_THREADS) {
-        const double dx = Xx[ob.first + p] - Rx, dy = Xy[ob.first + p] - Ry, dz = Xz[ob.first + p] - Rz;
-        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-        sh[p] = hx;
-        sh[nn + p] = hy;
-        sh[2 * nn + p] = hz;
-        sh[3 * nn + p] = (float)(dx - (double)hx);
-        sh[4 * nn + p] = (float)(dy - (double)hy);
-        sh[5 * nn + p] = (float)(dz - (double)hz);
-    }
-    __syncthreads();
+__host__ __device__ inline size_t ib_smem_bytes(int max_nodes) {
+    return (size_t)IB_SMEM_PER_NODE * max_nodes + IB_SMEM_TAIL;
+}
 
-    // ---- total area and volume (FP64 accumulation)
-    double sg = 0.0, vol = 0.0;
-    for (int t = threadIdx.x; t < T.nt; t += IB_THREADS) {
-        const int4 tr = T.tri[t];
-        const f3 eb = P.rel(tr.y, tr.x), ec = P.rel(tr.z, tr.x);
-        const f3 N = cross(eb, ec);
-        sg += 0.5 * (double)sqrtf(dot(N, N));
-        vol += (double)dot(P.pos(tr.x), N);
-    }
-    __shared__ double red[2][IB_THREADS / 32];
-    sg = warp_sum_d(sg);
-    vol = warp_sum_d(vol);
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = sg;
-        red[1][threadIdx.x >> 5] = vol;
-    }
-    __syncthreads();
-    sg = 0.0;
-    vol = 0.0;
+// Sum over a warp of FP32 values as an unevaluated hi + lo pair.
+__device__ __forceinline__ df warp_sum_df(df a) {
 #pragma unroll
-    for (int k = 0; k < IB_THREADS / 32; ++k) {
-        sg += red[0][k];
-        vol += red[1][k];
+    for (int o = 16; o > 0; o >>= 1) {
+        const df b{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, b);
     }
-    const double V = -vol / 6.0;
-    const float dSg = (float)((sg - T.Sg0) / sg);
-    const float dV = (float)((V - T.V0) / T.V0);
+    return a;
+}
 
+struct Forces {
+    float *x, *y, *z;
+    __device__ __forceinline__ void add(int p, f3 v) const {
+        atomicAdd(x + p, v.x);
+        atomicAdd(y + p, v.y);
+        atomicAdd(z + p, v.z);
+    }
+};
+
+__device__ __forceinline__ void edge_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
+    const int4 r = __ldg(T.edge + e);  // (a, b, L0 bits, 1/L0 bits)
+    const float L0 = __int_as_float(r.z), iL0 = __int_as_float(r.w);
+    const f3 d = P.rel(r.y, r.x);
+    const float il = rsqrtf(dot(d, d));
+    const float L = dot(d, d) * il;
+    const float lam = L * iL0;
+    float kap = 1.f;
+    if (T.nonlinear) {  // (lambda^0.5 + lambda^-2.5) / (lambda + lambda^-3)
+        const float sl = sqrtf(lam), il3 = 1.f / (lam * lam * lam);
+        kap = (sl + il3 * sl) / (lam + il3);
+    }
+    const f3 f = (T.ks * kap * (L - L0) * iL0 * il) * d;
+    F.add(r.x, f);
+    F.add(r.y, -1.f * f);
+}
+
+__device__ __forceinline__ void bending_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
+    const int4 q = __ldg(T.quad + e);  // (a, b, c, d): triangles (a,b,c) and (d,c,b)
+    const float ith0 = __ldg(T.inv_theta0 + e);
+    const f3 A = P.rel(q.x, q.y), C = P.rel(q.z, q.y), D = P.rel(q.w, q.y);  // relative to b
+    f3 n1 = cross(-1.f * A, C - A);  // (b-a) x (c-a)
+    f3 n2 = cross(C - D, -1.f * D);  // (c-d) x (b-d)
+    n1 = rsqrtf(dot(n1, n1)) * n1;
+    n2 = rsqrtf(dot(n2, n2)) * n2;
+    const f3 cr = cross(n1, n2);
+    const float alpha = atan2f(sqrtf(dot(cr, cr)), dot(n1, n2));
     const float PI_F = 3.14159265358979f;
-    for (int p = threadIdx.x; p < nn; p += IB_THREADS) {
-        f3 F = mk(0.f, 0.f, 0.f);
-        // stretching
-        if (T.ks != 0.f) {
-            for (int k = T.eoff[p]; k < T.eoff[p + 1]; ++k) {
-                const int2 r = T.erec[k];
-                const float L0 = __int_as_float(r.y);
-                const f3 d = P.rel(r.x, p);
-                const float L = sqrtf(dot(d, d));
-                const float lam = L / L0;
-                float kap = 1.f;
-                if (T.nonlinear) {
-                    const float sl = sqrtf(lam);
-                    kap = (sl + 1.f / (lam * lam * sl)) / (lam + 1.f / (lam * lam * lam));
-                }
-                F = F + (T.ks * kap * (L - L0) / (L0 * L)) * d;
-            }
-        }
-        // bending
-        if (T.kb != 0.f) {
-            for (int k = T.qoff[p]; k < T.qoff[p + 1]; ++k) {
-                const int4 id = T.qrec[k];
-                const float th0 = T.qth0[k];
-                const f3 A = P.rel(id.x, p), B = P.rel(id.y, p), C = P.rel(id.z, p), D = P.rel(id.w, p);
-                f3 n1 = cross(B - A, C - A);
-                f3 n2 = cross(C - D, B - D);
-                n1 = rsqrtf(dot(n1, n1)) * n1;
-                n2 = rsqrtf(dot(n2, n2)) * n2;
-                const f3 cr = cross(n1, n2);
-                const float alpha = atan2f(sqrtf(dot(cr, cr)), dot(n1, n2));
-                const float theta = dot(D - B, n1) > 0.f ? PI_F - alpha : PI_F + alpha;
-                const float sb = T.kb * (theta - th0) / th0;
-                if (id.x == p)
-                    F = F + sb * n1;
-                else
-                    F = F - (0.5f * sb) * (n1 + n2);
-            }
-        }
-        // local area, global area, volume
-        if (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) {
-            for (int k = T.toff[p]; k < T.toff[p + 1]; ++k) {
-                const int4 tr = T.trec[k];
-                const float S0 = __int_as_float(tr.w);
-                const f3 B = P.rel(tr.y, p), C = P.rel(tr.z, p);
-                const f3 N = cross(B, C);
-                const float nlen = sqrtf(dot(N, N));
-                const float S = 0.5f * nlen;
-                const f3 cen = (1.f / 3.f) * (B + C);  // centroid relative to the node
-                const f3 w = (-rsqrtf(dot(cen, cen))) * cen;
-                const float cw = -T.kal * (S - S0) / S - T.kag * dSg;
-                const float cv = T.kv * dV * S / (3.f * nlen);
-                F = F + cw * w + cv * N;
-            }
-        }
+    const float theta = dot(D, n1) > 0.f ? PI_F - alpha : PI_F + alpha;
+    const float sb = T.kb * (theta * ith0 - 1.f);
+    const f3 fa = sb * n1, fd = sb * n2;
+    const f3 fe = -0.5f * (fa + fd);
+    F.add(q.x, fa);
+    F.add(q.w, fd);
+    F.add(q.y, fe);
+    F.add(q.z, fe);
+}
 
-        // ---- coupling: interpolation, drag, spreading
-        const int i = ob.first + p;
-        double x = Xx[i], y = Xy[i], z = Xz[i];
-        double vx = Vx[i], vy = Vy[i], vz = Vz[i];
-        Corners c;
-        corners(s, x, y, z, c);
-        float ux = 0.f, uy = 0.f, uz = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (c.f[k] >= 0) {
-                const float4 u = s.ufield[c.f[k]];
-                ux += c.w[k] * u.x;
-                uy += c.w[k] * u.y;
-                uz += c.w[k] * u.z;
-            }
-        }
-        const double fdx = s.xi * ((double)ux - vx);
-        const double fdy = s.xi * ((double)uy - vy);
-        const double fdz = s.xi * ((double)uz - vz);
-        const float gx = (float)-fdx, gy = (float)-fdy, gz = (float)-fdz;
-        float dropx = 0.f, dropy = 0.f, dropz = 0.f;
-        float4 *G = s.G[par];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (c.f[k] >= 0) {
-                atomicAdd(G + c.f[k], make_float4(c.w[k] * gx, c.w[k] * gy, c.w[k] * gz, 0.f));
-                mark(s.gmask[par], c.f[k]);
-            } else {
-                dropx += c.w[k] * gx;
-                dropy += c.w[k] * gy;
-                dropz += c.w[k] * gz;
-            }
-        }
-        if (dropx != 0.f || dropy != 0.f || dropz != 0.f) {
-            atomicAdd(s.dropped, (double)dropx);
-            atomicAdd(s.dropped + 1, (double)dropy);
-            atomicAdd(s.dropped + 2, (double)dropz);
-        }
+__device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, int t, float dSg, float dV,
+                                               const Forces &F) {
+    const int4 tr = __ldg(T.tri + t);  // (a, b, c, S0 bits), inward
+    const float S0 = __int_as_float(tr.w);
+    const f3 B = P.rel(tr.y, tr.x), C = P.rel(tr.z, tr.x);  // relative to a
+    const f3 N = cross(B, C);
+    const float inl = rsqrtf(dot(N, N));
+    const float S = 0.5f * dot(N, N) * inl;
+    const f3 G = (1.f / 3.f) * (B + C);  // centroid relative to a
+    const float cw = -T.kal * (S - S0) / S - T.kag * dSg;  // local + global area
+    const f3 fv = (T.kv * dV * S * inl / 3.f) * N;          // volume, a third per vertex
+    const f3 wa = -1.f * G, wb = B - G, wc = C - G;
+    F.add(tr.x, (cw * rsqrtf(dot(wa, wa))) * wa + fv);
+    F.add(tr.y, (cw * rsqrtf(dot(wb, wb))) * wb + fv);
+    F.add(tr.z, (cw * rsqrtf(dot(wc, wc))) * wc + fv);
+}
 
-        // ---- Newton update
-        const double im = 1.0 / ob.mass;
-        const double *fe = s.fext + 3 * o;
-        vx += ((double)F.x + fdx + fe[0]) * im;
-        vy += ((double)F.y + fdy + fe[1]) * im;
-        vz += ((double)F.z + fdz + fe[2]) * im;
-        x += vx;
-        y += vy;
-        z += vz;
-        Vx[i] = vx;
-        Vy[i] = vy;
-        Vz[i] = vz;
-        Xx[i] = x;
-        Xy[i] = y;
-        Xz[i] = z;
-        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
-            atomicOr(s.status, ST_NODE_NAN);
+// Coupling and Newton update of node i (global index) of object o under the
+// membrane force F.
+__device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F, float inv_mass, int par) {
+    const int NN = s.nn_total;
+    float *Xh = s.Xh, *Xl = s.Xl, *Vh = s.Vh, *Vl = s.Vl;
+    df x{Xh[i], Xl[i]}, y{Xh[NN + i], Xl[NN + i]}, z{Xh[2 * NN + i], Xl[2 * NN + i]};
+    df vx{Vh[i], Vl[i]}, vy{Vh[NN + i], Vl[NN + i]}, vz{Vh[2 * NN + i], Vl[2 * NN + i]};
+    Corners c;
+    corners(s, x, y, z, c);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (c.f[k] >= 0) {
+            const float4 u = s.ufield[c.f[k]];
+            ux += c.w[k] * u.x;
+            uy += c.w[k] * u.y;
+            uz += c.w[k] * u.z;
+        }
+    }
+    const float xi = s.xi;
+    const float fdx = xi * ((ux - vx.hi) - vx.lo);
+    const float fdy = xi * ((uy - vy.hi) - vy.lo);
+    const float fdz = xi * ((uz - vz.hi) - vz.lo);
+    float dropx = 0.f, dropy = 0.f, dropz = 0.f;
+    float4 *G = s.G[par];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float w = c.w[k];
+        if (c.f[k] >= 0) {
+            atomicAdd(G + c.f[k], make_float4(-w * fdx, -w * fdy, -w * fdz, 0.f));
+            mark(s.gmask[par], c.f[k]);
         } else {
-            corners(s, x, y, z, c);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c.f[k] >= 0) mark(s.umask, c.f[k]);
+            dropx -= w * fdx;
+            dropy -= w * fdy;
+            dropz -= w * fdz;
         }
+    }
+    if (dropx != 0.f || dropy != 0.f || dropz != 0.f) {
+        atomicAdd(s.dropped, (double)dropx);
+        atomicAdd(s.dropped + 1, (double)dropy);
+        atomicAdd(s.dropped + 2, (double)dropz);
+    }
+    const float *fe = s.fext + 3 * o;
+    vx = df_add_f(vx, (F.x + fdx + fe[0]) * inv_mass);
+    vy = df_add_f(vy, (F.y + fdy + fe[1]) * inv_mass);
+    vz = df_add_f(vz, (F.z + fdz + fe[2]) * inv_mass);
+    x = df_add(x, vx);
+    y = df_add(y, vy);
+    z = df_add(z, vz);
+    Vh[i] = vx.hi;
+    Vl[i] = vx.lo;
+    Vh[NN + i] = vy.hi;
+    Vl[NN + i] = vy.lo;
+    Vh[2 * NN + i] = vz.hi;
+    Vl[2 * NN + i] = vz.lo;
+    Xh[i] = x.hi;
+    Xl[i] = x.lo;
+    Xh[NN + i] = y.hi;
+    Xl[NN + i] = y.lo;
+    Xh[2 * NN + i] = z.hi;
+    Xl[2 * NN + i] = z.lo;
+    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) {
+        atomicOr(s.status, ST_NODE_NAN);
+    } else {
+        corners(s, x, y, z, c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c.f[k] >= 0) mark(s.umask, c.f[k]);
     }
 }
 
+// Share [r n / C, (r+1) n / C) of n items for cluster rank r.
+__device__ __forceinline__ int share_lo(int n, int r, int C) { return (int)(((long long)n * r) / C); }
+
+// The whole update of object o by the calling cluster (all C blocks call it).
+__device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int par, float *sh) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const ObjDev ob = s.obj[o];
+    const TplDev &T = s.tpl[ob.tid];
+    const int nn = ob.nn, f0 = ob.first, NN = s.nn_total;
+
+    float *Fx = sh + 6 * nn, *Fy = sh + 7 * nn, *Fz = sh + 8 * nn;
+    float *tail = sh + 9 * nn;  // [0..3] this block's area / volume partials, [4..5] factors
+    const Stage P{sh, sh + nn, sh + 2 * nn, sh + 3 * nn, sh + 4 * nn, sh + 5 * nn};
+    const Forces F{Fx, Fy, Fz};
+
+    // 1. stage positions relative to the first node, clear the forces
+    for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const df a{s.Xh[k * NN + f0 + p], s.Xl[k * NN + f0 + p]};
+            const df b{s.Xh[k * NN + f0], s.Xl[k * NN + f0]};
+            const df d = df_add(a, {-b.hi, -b.lo});
+            sh[k * nn + p] = d.hi;
+            sh[(3 + k) * nn + p] = d.lo;
+        }
+        Fx[p] = 0.f;
+        Fy[p] = 0.f;
+        Fz[p] = 0.f;
+    }
+    __syncthreads();
+
+    // 2. this block's share of the area and volume sums
+    df area{0.f, 0.f}, vol{0.f, 0.f};
+    if (T.kag != 0.f || T.kv != 0.f) {
+        for (int t = share_lo(T.nt, r, C) + threadIdx.x; t < share_lo(T.nt, r + 1, C); t += blockDim.x) {
+            const int4 tr = __ldg(T.tri + t);
+            const f3 N = cross(P.rel(tr.y, tr.x), P.rel(tr.z, tr.x));
+            area = df_add_f(area, 0.5f * sqrtf(dot(N, N)));
+            vol = df_add_f(vol, dot(P.pos(tr.x), N));
+        }
+    }
+    __shared__ df wpart[2][IB_THREADS / 32];
+    area = warp_sum_df(area);
+    vol = warp_sum_df(vol);
+    if ((threadIdx.x & 31) == 0) {
+        wpart[0][threadIdx.x >> 5] = area;
+        wpart[1][threadIdx.x >> 5] = vol;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        df t = wpart[threadIdx.x][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = df_add(t, wpart[threadIdx.x][w]);
+        tail[2 * threadIdx.x] = t.hi;
+        tail[2 * threadIdx.x + 1] = t.lo;
+    }
+    cl.sync();  // staging, cleared forces and partial sums visible in the cluster
+
+    // totals of the object in FP64, partials taken in rank order
+    if (threadIdx.x == 0) {
+        double Sg = 0.0, V6 = 0.0;
+        for (int j = 0; j < C; ++j) {
+            const float *pj = cl.map_shared_rank(tail, j);
+            Sg += (double)pj[0] + (double)pj[1];
+            V6 += (double)pj[2] + (double)pj[3];
+        }
+        // differences to the relaxed state in FP64, ratios in FP32
+        const float dS = (float)(Sg - T.Sg0), dVol = (float)(V6 * (-1.0 / 6.0) - T.V0);
+        tail[4] = (T.kag != 0.f) ? dS / (float)Sg : 0.f;
+        tail[5] = (T.kv != 0.f) ? dVol / (float)T.V0 : 0.f;
+    }
+    __syncthreads();
+    const float dSg = tail[4], dV = tail[5];
+
+    // 3. this block's share of the elements [edges | pairs | triangles]
+    const int ne = (T.ks != 0.f) ? T.ne : 0;
+    const int nq = (T.kb != 0.f) ? T.ne : 0;
+    const int nt = (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) ? T.nt : 0;
+    const int M = ne + nq + nt;
+    for (int k = share_lo(M, r, C) + threadIdx.x; k < share_lo(M, r + 1, C); k += blockDim.x) {
+        if (k < ne)
+            edge_force(T, P, k, F);
+        else if (k < ne + nq)
+            bending_force(T, P, k - ne, F);
+        else
+            triangle_force(T, P, k - ne - nq, dSg, dV, F);
+    }
+    cl.sync();  // every block's partial forces complete
+
+    // 4. this block's share of the nodes: forces summed over the cluster in
+    //    rank order, then coupling and update
+    for (int p = share_lo(nn, r, C) + threadIdx.x; p < share_lo(nn, r + 1, C); p += blockDim.x) {
+        f3 Fp = mk(0.f, 0.f, 0.f);
+        for (int j = 0; j < C; ++j) {
+            const float *Fj = cl.map_shared_rank(sh, j) + 6 * nn;
+            Fp = Fp + mk(Fj[p], Fj[nn + p], Fj[2 * nn + p]);
+        }
+        node_update(s, o, f0 + p, Fp, ob.inv_mass, par);
+    }
+    cl.sync();  // remote reads complete before any block reuses its shared memory
+}
 
 }  // namespace lbib

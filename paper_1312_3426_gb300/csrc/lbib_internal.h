@@ -17,8 +17,10 @@
 //                    only at cells whose bit is set in umask: the 8 lattice
 //                    nodes around every node position, marked by the node
 //                    update of the same step and read by the next one.
-//   nodes            X[3][nn_total], V[3][nn_total] FP64, structure of
-//                    arrays, objects contiguous in id order.
+//   nodes            positions and velocities as unevaluated sums of two
+//                    FP32 numbers (hi + lo, about 48 significant bits):
+//                    Xh, Xl, Vh, Vl each [3][nn_total], structure of arrays,
+//                    objects contiguous in id order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,7 +33,7 @@ namespace lbib {
 constexpr int NQ = 19;
 constexpr int FLUID_THREADS = 256;
 constexpr int IB_THREADS = 256;
-constexpr int MAX_TEMPLATE_NODES = 8192;
+constexpr int MAX_TEMPLATE_NODES = 6144;  // 9 floats of shared memory per node
 
 // D3Q19 directions of this library: rest, the 6 axis directions in +/- pairs,
 // then the 12 face diagonals in +/- pairs; opposite(q) = q+1 for odd q,
@@ -58,32 +60,28 @@ enum : uint32_t {
     ST_TIMEOUT = 4u,      // a bounded device-side wait gave up
 };
 
-// Per-node incidence records of one template (node-centric gather).
-//   erec: (neighbour id, rest length as float bits)
-//   qrec: the 4 node ids (a,b,c,d) of a bending pair, rotated so that the
-//         node owning the record is a (apex of the first triangle) or b (on
-//         the shared edge); (a,b,c) and (d,c,b) are the inward cyclic
-//         orders of the two triangles.  qth0: rest angle of that edge.
-//   trec: the triangle's ids as a cyclic rotation starting at the owner,
-//         .w = rest area as float bits.
+// Element lists of one template (device), all node ids local to an object:
+//   tri:        (a, b, c, rest area S0 as float bits), inward-ordered as given
+//   edge:       (a, b, rest length L0, 1/L0 as float bits), a < b,
+//               lexicographic
+//   quad:       (a, b, c, d) for edge (b, c): (a,b,c) and (d,c,b) are the
+//               inward cyclic orders of the two triangles sharing it;
+//               inv_theta0: 1 / its rest inner angle
 struct TplDev {
-    int nn, nt;
+    int nn, nt, ne;
     float ks, kb, kal, kag, kv;
     int nonlinear;
     double Sg0, V0;
-    const int4 *tri;      // [nt] (a, b, c, 0) as given, inward
-    const int *eoff;      // [nn+1]
-    const int2 *erec;
-    const int *qoff;      // [nn+1]
-    const int4 *qrec;
-    const float *qth0;
-    const int *toff;      // [nn+1]
-    const int4 *trec;
+    const int4 *tri;
+    const int4 *edge;
+    const int4 *quad;
+    const float *inv_theta0;
 };
 
+// One object: its template, first global node, node count and 1/m.
 struct ObjDev {
-    int tid, first, nn, pad;
-    double mass;
+    int tid, first, nn;
+    float inv_mass;
 };
 
 // Everything a kernel needs to know about one simulation (POD, passed by
@@ -95,39 +93,35 @@ struct SimDev {
     float omega, fpre, rho0;  // 1/tau, 1 - 1/(2 tau), rest density
     float gx, gy, gz;         // body force
     float scale, inv_scale;   // 2^s, 2^-s
-    double xi;
+    float xi;
     void *pop[2];
     float4 *G[2];
     uint32_t *gmask[2];
     uint32_t *umask;
     float4 *ufield;
-    double *X, *V;            // [3][nn_total]
+    float *Xh, *Xl, *Vh, *Vl; // [3][nn_total] each
     int nn_total, nobj;
     const ObjDev *obj;
-    const double *fext;       // [nobj][3] external force per node of each object
+    const float *fext;        // [nobj][3] external force per node of each object
     const TplDev *tpl;
     uint32_t *status;
     double *dropped;          // [3]
 };
 
 // ---- launchers (fluid.cu) -------------------------------------------------
-cudaError_t launch_fluid(const SimDev &s, int par, cudaStream_t st);
+cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);
 cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
                           cudaStream_t st);
+cudaError_t launch_read_coupling(const SimDev &s, int gpar, float *g_full, cudaStream_t st);
+cudaError_t launch_set_coupling(const SimDev &s, int gpar, const float *g_full, cudaStream_t st);
 cudaError_t launch_read_pops(const SimDev &s, int pop_par, double *h_full, cudaStream_t st);
 cudaError_t launch_set_pops(const SimDev &s, int pop_par, const double *h_full, cudaStream_t st);
 cudaError_t launch_mass(const SimDev &s, int pop_par, double *acc, cudaStream_t st);
 
 // ---- launchers (ib.cu) -----------------------------------------------------
-cudaError_t ib_configure(int max_nodes);
-cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, cudaStream_t st);
+// one cluster of `cluster` blocks per object; max_nodes sizes shared memory
+cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cudaStream_t st);
 // oid >= 0: one object into out[14]; oid < 0: every object into out[nobj][14]
 cudaError_t launch_analyze(const SimDev &s, int oid, double *out, cudaStream_t st);
-
-// ---- batched persistent step (batch.cu) -----------------------------------
-cudaError_t launch_batch_ib(const SimDev *sims_dev, const int4 *items, int n_items, int max_nodes,
-                            int par, int grid, cudaStream_t st);
-cudaError_t launch_batch_fluid(const SimDev *sims_dev, const int *sim_of_block, const int *first_block,
-                               int n_blocks, int prec, int par, int grid, unsigned *ticket, cudaStream_t st);
 
 }  // namespace lbib

@@ -27,7 +27,6 @@ struct lbib_sim {
     std::vector<void *> tpl_mem;        // device records of every template
     size_t tpl_bytes = 0;
     int max_nodes = 0;                  // largest template
-    int configured_nodes = 0;           // shared-memory limit set for it
 
     std::vector<lbib::ObjDev> objs;
     int nn_total = 0;
@@ -35,13 +34,15 @@ struct lbib_sim {
     bool host_newer = false;     // host mirror changed since the last upload
     bool dev_newer = false;      // device state advanced since the last download
     bool tables_dirty = false;   // object/template tables need an upload
-    double *dX = nullptr, *dV = nullptr;
+    float *dnodes = nullptr;     // Xh, Xl, Vh, Vl, each [3][nn_total]
     int dev_nn_cap = 0;
     size_t node_bytes = 0;
     lbib::ObjDev *d_obj = nullptr;
     lbib::TplDev *d_tpl = nullptr;
-    std::vector<double> fext;    // [nobj][3]
-    double *d_fext = nullptr;
+    std::vector<float> fext;     // [nobj][3]
+    std::vector<double> masses;
+    float *d_fext = nullptr;
+    int cluster = 4;             // thread blocks per object in the object kernel
     bool fext_dirty = false;
     double *d_analyze = nullptr; // [nobj][14] read-out buffer
     int d_obj_cap = 0;

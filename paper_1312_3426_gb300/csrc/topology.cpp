@@ -4,8 +4,7 @@
 //   - for every edge (b,c) its bending pair (a,b,c,d): a is the third node
 //     of the triangle that runs b->c, d that of the triangle that runs c->b,
 //   - the relaxed lengths L0, inner angles theta0, triangle areas S0, total
-//     area S_g0 and volume V0 of the (stretched) template geometry, in FP64,
-//   - node-centric incidence lists used by the device gather.
+//     area S_g0 and volume V0 of the (stretched) template geometry, in FP64.
 // It rejects meshes that are not closed, consistently ordered 2-manifolds,
 // meshes with unused nodes or degenerate triangles, and meshes whose
 // triangles point outward (the library requires AB x AC to point inside).
@@ -160,63 +159,6 @@ bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, cons
         return false;
     }
 
-    // node-centric incidence lists
-    std::vector<int> ne(nn, 0), nq(nn, 0), ntc(nn, 0);
-    for (int e = 0; e < T.ne; ++e) {
-        ne[T.edges[2 * e]]++;
-        ne[T.edges[2 * e + 1]]++;
-        for (int k = 0; k < 4; ++k) nq[T.quads[4 * e + k]]++;
-    }
-    for (int t = 0; t < nt; ++t)
-        for (int k = 0; k < 3; ++k) ntc[T.tri[3 * t + k]]++;
-    auto prefix = [nn](const std::vector<int> &cnt, std::vector<int> &off) {
-        off.assign(nn + 1, 0);
-        for (int i = 0; i < nn; ++i) off[i + 1] = off[i] + cnt[i];
-    };
-    prefix(ne, T.eoff);
-    prefix(nq, T.qoff);
-    prefix(ntc, T.toff);
-    T.erec.assign(2 * (size_t)T.eoff[nn], 0);
-    T.qrec.assign(4 * (size_t)T.qoff[nn], 0);
-    T.qth0.assign(T.qoff[nn], 0.f);
-    T.trec.assign(4 * (size_t)T.toff[nn], 0);
-    std::vector<int> fe(T.eoff.begin(), T.eoff.end() - 1), fq(T.qoff.begin(), T.qoff.end() - 1),
-        ft(T.toff.begin(), T.toff.end() - 1);
-    auto fbits = [](float f) {
-        int32_t i;
-        std::memcpy(&i, &f, sizeof(i));
-        return i;
-    };
-    for (int e = 0; e < T.ne; ++e) {
-        const int a = T.edges[2 * e], b = T.edges[2 * e + 1];
-        const int32_t l0 = fbits((float)T.L0[e]);
-        int k = fe[a]++;
-        T.erec[2 * k] = b;
-        T.erec[2 * k + 1] = l0;
-        k = fe[b]++;
-        T.erec[2 * k] = a;
-        T.erec[2 * k + 1] = l0;
-        const int *q = &T.quads[4 * e];
-        const int fwd[4] = {q[0], q[1], q[2], q[3]}, bwd[4] = {q[3], q[2], q[1], q[0]};
-        for (int r = 0; r < 4; ++r) {
-            const int owner = q[r];
-            const int *ids = (r == 0 || r == 1) ? fwd : bwd;
-            k = fq[owner]++;
-            for (int m = 0; m < 4; ++m) T.qrec[4 * k + m] = ids[m];
-            T.qth0[k] = (float)T.theta0[e];
-        }
-    }
-    for (int t = 0; t < nt; ++t) {
-        const int32_t s0 = fbits((float)T.S0[t]);
-        for (int r = 0; r < 3; ++r) {
-            const int owner = T.tri[3 * t + r];
-            const int k = ft[owner]++;
-            T.trec[4 * k] = owner;
-            T.trec[4 * k + 1] = T.tri[3 * t + (r + 1) % 3];
-            T.trec[4 * k + 2] = T.tri[3 * t + (r + 2) % 3];
-            T.trec[4 * k + 3] = s0;
-        }
-    }
     return true;
 }
 

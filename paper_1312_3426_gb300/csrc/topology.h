@@ -16,12 +16,6 @@ struct Topology {
     std::vector<int> quads;                   // [ne][4] (a, b, c, d)
     std::vector<double> L0, theta0, S0;       // [ne], [ne], [nt]
     double Sg0 = 0.0, V0 = 0.0;
-    // node-centric incidence (CSR over nodes)
-    std::vector<int> eoff, qoff, toff;        // [nn+1]
-    std::vector<int32_t> erec;                // [2 * eoff[nn]]  (neighbour, L0 bits)
-    std::vector<int32_t> qrec;                // [4 * qoff[nn]]  (a, b, c, d), owner = a or b
-    std::vector<float> qth0;                  // [qoff[nn]]
-    std::vector<int32_t> trec;                // [4 * toff[nn]]  (owner, next, next, S0 bits)
 };
 
 bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],

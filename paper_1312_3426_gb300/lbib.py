@@ -72,6 +72,8 @@ def load(path: str = LIB_PATH):
         "lbib_read_velocity": (st, [P, P, C.c_int64]),
         "lbib_read_density": (st, [P, P, C.c_int64]),
         "lbib_read_populations": (st, [P, P, C.c_int64]),
+        "lbib_read_coupling_force": (st, [P, P, C.c_int64]),
+        "lbib_set_coupling_force": (st, [P, P, C.c_int64]),
         "lbib_set_populations": (st, [P, P, C.c_int64]),
         "lbib_object_analyze": (st, [P, C.c_int, P]),
         "lbib_fluid_mass": (st, [P, P]),
@@ -83,6 +85,8 @@ def load(path: str = LIB_PATH):
         "lbib_objects_set_force": (st, [P, P, C.c_int]),
         "lbib_objects_analyze": (st, [P, P, C.c_int64]),
         "lbib_profile_enable": (st, [P, C.c_int]),
+        "lbib_set_tuning": (st, [P, C.c_int, C.c_int]),
+        "lbib_get_tuning": (st, [P, C.c_int, C.POINTER(C.c_int)]),
         "lbib_profile_read": (st, [P, P]),
         "lbib_abi_version": (C.c_int, []),
     }
@@ -233,6 +237,17 @@ def lbib_read_density(h, nx, ny, nz):
     return r
 
 
+def lbib_read_coupling_force(h, nx, ny, nz):
+    g = np.zeros((3, nz, ny, nx), np.float32)
+    _check(h, _lib.lbib_read_coupling_force(h, _p(g), g.size))
+    return g
+
+
+def lbib_set_coupling_force(h, g):
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    _check(h, _lib.lbib_set_coupling_force(h, _p(g), g.size))
+
+
 def lbib_read_populations(h, nx, ny, nz):
     f = np.empty((19, nz, ny, nx), np.float64)
     _check(h, _lib.lbib_read_populations(h, _p(f), f.size))
@@ -259,6 +274,19 @@ def lbib_objects_analyze(h, n_obj, out=None):
     out = out if out is not None else np.zeros((n_obj, 14))
     _check(h, _lib.lbib_objects_analyze(h, _p(out), int(n_obj)))
     return out
+
+
+LBIB_TUNE_IB_CLUSTER = 0
+
+
+def lbib_set_tuning(h, key, value):
+    _check(h, _lib.lbib_set_tuning(h, int(key), int(value)))
+
+
+def lbib_get_tuning(h, key):
+    v = C.c_int()
+    _check(h, _lib.lbib_get_tuning(h, int(key), C.byref(v)))
+    return v.value
 
 
 def lbib_profile_enable(h, on=True):
@@ -401,6 +429,12 @@ class Sim:
 
     def density(self):
         return lbib_read_density(self.h, self.nx, self.ny, self.nz)
+
+    def coupling_force(self):
+        return lbib_read_coupling_force(self.h, self.nx, self.ny, self.nz)
+
+    def set_coupling_force(self, g):
+        lbib_set_coupling_force(self.h, g)
 
     def populations(self):
         return lbib_read_populations(self.h, self.nx, self.ny, self.nz)

@@ -9,8 +9,8 @@ Recipes (stand-ins for the paper's red-blood-cell channel, Sec. 6-7, whose
 mesh and geometry files are not available):
 
   * ``channel_sphere``  40x20x20 channel, walls at y=0 and y=19, tau=1,
-    rho0=1, body force 1e-5 along x, one level-2 icosphere of radius 4 at
-    the box centre, ks=0.1 kb=0.03 kal=0.1 kag=0.4 kv=1.0 (the moduli of the
+    rho0=1, body force 1e-5 along x, drag 0.05 per step, node mass 1, one
+    level-2 icosphere of radius 4 at the box centre, ks=0.1 kb=0.03 kal=0.1 kag=0.4 kv=1.0 (the moduli of the
     paper's feature table), nonlinear stretching; 1000 steps.
   * ``channel_rbc``     256x128x128 channel, same fluid, 200 Evans-Fung red
     blood cells (level-3 icosphere mapped to the biconcave profile, radius 8)
@@ -69,7 +69,10 @@ class Scene:
     tau: float = 1.0
     rho0: float = 1.0
     body_force: tuple = (1e-5, 0.0, 0.0)
-    friction: float = 0.5
+    # drag coefficient per lattice step: the paper's example pairs friction
+    # 0.5 with an integration time step of 0.1 (Sec. 6), i.e. a momentum
+    # exchange of 0.05 of the relative velocity per step for unit node mass
+    friction: float = 0.05
     steps: int = 1000
     templates: list = field(default_factory=list)
     objects: list = field(default_factory=list)
