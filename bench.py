@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ib-cluster", type=int, default=0, help="thread blocks per object (0: library default)")
+    ap.add_argument("--launch", choices=["separate", "persistent"], default="separate",
+                    help="one launch per phase (lbib_step) or one persistent launch per step (lbib_batch_step)")
     return ap.parse_args()
 
 
@@ -239,13 +241,18 @@ def main():
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
-    lbib.lbib_profile_enable(sim.h, True)
+    persistent = args.launch == "persistent"
+    if not persistent:
+        lbib.lbib_profile_enable(sim.h, True)
     e0.record(stream)
-    sim.step(args.steps)
+    if persistent:
+        lbib.lbib_batch_step([sim.h], args.steps)
+    else:
+        sim.step(args.steps)
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
-    prof = lbib.lbib_profile_read(sim.h)
+    prof = lbib.lbib_profile_read(sim.h) if not persistent else None
     lbib.lbib_profile_enable(sim.h, False)
     sim.sync()
     ms = e0.elapsed_time(e1)
@@ -255,8 +262,12 @@ def main():
     ms = float(t.item())
     value = world * nf * args.steps / (ms / 1e3) / 1e6
 
-    fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
-    ib_ms = prof["ib_ms"] / max(1, prof["ib_launches"])
+    if prof is not None:
+        fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
+        ib_ms = prof["ib_ms"] / max(1, prof["ib_launches"])
+    else:  # one fused launch per step: the whole step is the kernel
+        fluid_ms = ms / args.steps
+        ib_ms = 0.0
     peak, peak_kind = measured_peak()
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * nf / (fluid_ms / 1e3) / 1e9
@@ -302,12 +313,13 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": f"k_fluid<{args.precision}>", "bytes_per_cell": bpc,
+                         "kernel": "k_batch_step" if persistent else f"k_fluid<{args.precision}>",
+                         "bytes_per_cell": bpc,
                          "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
             "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "ib": round(ib_ms, 5)},
             "nodes_per_s": round(world * sc.n_nodes * args.steps / (ms / 1e3), 1),
             "step_hbm_frac": round((bpc * nf + 400 * sc.n_nodes) / (ms / args.steps / 1e3) / 1e9 / peak, 4),
-            "gpu_launches": args.steps * (2 if sc.objects else 1),
+            "gpu_launches": args.steps * (1 if persistent else (2 if sc.objects else 1)),
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": base,

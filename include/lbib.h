@@ -107,7 +107,7 @@ LBIB_API const char *lbib_last_error(const lbib_sim *sim);
  * (else kappa = 1).  Relaxed lengths, angles, areas, total area and volume
  * are measured on the stretched geometry.  Errors: LBIB_ERR_ID,
  * LBIB_ERR_MESH (open, non-manifold, inconsistent or outward-ordered),
- * LBIB_ERR_ARG (n_nodes > 6144 or < 4). */
+ * LBIB_ERR_ARG (n_nodes > 5120 or < 4). */
 LBIB_API lbib_status lbib_template_create(lbib_sim *sim, int tid, const double *nodes_xyz, int n_nodes,
                                  const int32_t *tris, int n_tris, const double stretch[3],
                                  double ks, double kb, double kal, double kag, double kv,

@@ -6,8 +6,11 @@
 // atomic ticket (rank 0 draws it and the cluster reads it through
 // distributed shared memory) and updates them as in ib_core.cuh.  Phase B:
 // once the objects are handed out, every block takes blocks of
-// FLUID_THREADS fluid cells, of any simulation, from a second ticket; a
-// fluid block of simulation s first waits until all of s's objects are done.
+// FLUID_THREADS fluid cells, of any simulation, from a second ticket.  A warp
+// whose 32 cells include active cells (cells near objects, see
+// lbib_internal.h) first waits until all of its simulation's objects are
+// done; the other warps need nothing from this step's object update and run
+// while it is still in progress.
 // Every object was handed out to a running cluster before any block reached
 // phase B, and objects never wait, so every wait ends; it is nevertheless
 // bounded, and on expiry the block flags the simulation (ST_TIMEOUT,
@@ -68,25 +71,34 @@ __global__ void __launch_bounds__(FLUID_THREADS) k_batch_step(const SimDev *__re
         const int2 it = fl_items[k];
         const SimDev s = sims[it.x];
         const int par = (par_base[it.x] + step_off) & 1;
-        if (threadIdx.x == 0) {
-            const volatile unsigned *done = counters + 2 + it.x;
-            const unsigned want = (unsigned)need[it.x];
-            unsigned spins = 0;
-            while (*done < want) {
-                __nanosleep(64);
-                if (++spins > BATCH_WAIT_SPINS) {
-                    atomicOr(s.status, ST_TIMEOUT);
-                    break;
+        const int f = it.y * FLUID_THREADS + (int)threadIdx.x;
+        const uint32_t act = active_word(s, f);  // warp-uniform
+        if (act) {
+            // cells near objects need this step's spread force: wait for the
+            // simulation's objects (warps without such cells go ahead)
+            if ((threadIdx.x & 31) == 0) {
+                const volatile unsigned *done = counters + 2 + it.x;
+                const unsigned want = (unsigned)need[it.x];
+                unsigned spins = 0;
+                while (*done < want) {
+                    __nanosleep(64);
+                    if (++spins > BATCH_WAIT_SPINS) {
+                        atomicOr(s.status, ST_TIMEOUT);
+                        break;
+                    }
                 }
+                __threadfence();
             }
-            __threadfence();
+            __syncwarp();
         }
-        __syncthreads();
-        const uint32_t seed = step_seed(t_base[it.x] + step_off);
-        switch (s.prec) {
-            case LBIB_POP_F32: fluid_block<float>(s, par, it.y * FLUID_THREADS, seed); break;
-            case LBIB_POP_F16S: fluid_block<__half>(s, par, it.y * FLUID_THREADS, seed); break;
-            default: fluid_block<__nv_bfloat16>(s, par, it.y * FLUID_THREADS, seed); break;
+        if (f < s.nf) {
+            const uint32_t seed = step_seed(t_base[it.x] + step_off);
+            const bool a = (act >> (threadIdx.x & 31)) & 1u;
+            switch (s.prec) {
+                case LBIB_POP_F32: fluid_cell<float>(s, par, f, a, seed); break;
+                case LBIB_POP_F16S: fluid_cell<__half>(s, par, f, a, seed); break;
+                default: fluid_cell<__nv_bfloat16>(s, par, f, a, seed); break;
+            }
         }
     }
 }
@@ -252,6 +264,11 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     cfg.numAttrs = 1;
     const int2 *fl_items = g_plan.d_items + g_plan.n_ib;
     for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            if (sims[i]->since_mark >= ACTIVE_RESET_STEPS) e = sim_remark(sims[i], st);
+            sims[i]->since_mark++;
+        }
+        if (e != cudaSuccess) break;
         e = cudaMemsetAsync(g_plan.d_counters, 0, (n + 2) * sizeof(unsigned), st);
         if (e != cudaSuccess) break;
         e = cudaLaunchKernelEx(&cfg, k_batch_step, (const SimDev *)g_plan.d_sims, (const int *)g_plan.d_par,

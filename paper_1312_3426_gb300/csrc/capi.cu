@@ -26,7 +26,7 @@ size_t pop_elem_bytes(int prec) { return prec == LBIB_POP_F32 ? 4 : 2; }
 
 struct FluidLayout {
     int nyf, nf, nfp, nwords;
-    size_t off_pop[2], off_G[2], off_gmask[2], off_umask, off_ufield, off_status, off_dropped, total;
+    size_t off_pop[2], off_G[2], off_amask, off_ufield, off_status, off_dropped, total;
 };
 
 bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
@@ -40,8 +40,7 @@ bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
     const size_t popb = (size_t)NQ * L.nfp * pop_elem_bytes(p.precision);
     for (int k = 0; k < 2; ++k) { L.off_pop[k] = o; o = align_up(o + popb, 256); }
     for (int k = 0; k < 2; ++k) { L.off_G[k] = o; o = align_up(o + (size_t)L.nf * 16, 256); }
-    for (int k = 0; k < 2; ++k) { L.off_gmask[k] = o; o = align_up(o + (size_t)L.nwords * 4, 256); }
-    L.off_umask = o; o = align_up(o + (size_t)L.nwords * 4, 256);
+    L.off_amask = o; o = align_up(o + (size_t)L.nwords * 4, 256);
     L.off_ufield = o; o = align_up(o + (size_t)L.nf * 16, 256);
     L.off_status = o; o = align_up(o + 4, 256);
     L.off_dropped = o; o = align_up(o + 24, 256);
@@ -203,8 +202,10 @@ lbib_status sim_upload(lbib_sim *s) {
         s->d.Vl = s->dnodes + 3 * n3;
         s->d.nn_total = nn;
         s->host_newer = false;
-        // the velocity samples must be valid at the (new) node corners
+        // the velocity samples must be valid at the (new) node corners, and
+        // the active cells must follow the nodes
         if (!(s->t == 0 && s->gmode == -1)) s->ufield_stale = true;
+        s->mark_stale = true;
     }
     return LBIB_OK;
 }
@@ -217,7 +218,25 @@ lbib_status sim_prepare_step(lbib_sim *s) {
         LBIB_CUDA(s, launch_fields(s->d, (int)(s->t & 1), s->gmode, nullptr, nullptr, 1, s->stream), "velocity samples");
         s->ufield_stale = false;
     }
+    if (s->mark_stale) {
+        // nodes may have moved arbitrarily: the buffer the next step clears
+        // holds forces at cells that may no longer be active
+        FluidLayout L;
+        fluid_layout(s->p, L);
+        LBIB_CUDA(s, cudaMemsetAsync((char *)s->fluid_mem + L.off_G[(s->t + 1) & 1], 0, (size_t)L.nf * 16, s->stream),
+                  "coupling force");
+        LBIB_CUDA(s, sim_remark(s, s->stream), "active cells");
+        s->mark_stale = false;
+    }
     return LBIB_OK;
+}
+
+// Clears the active-cell mask and marks the cells around every node.
+cudaError_t sim_remark(lbib_sim *s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(s->d.amask, 0, (size_t)s->d.nwords * 4, st);
+    if (e == cudaSuccess) e = launch_mark_all(s->d, st);
+    s->since_mark = 0;
+    return e;
 }
 
 }  // namespace lbib
@@ -292,9 +311,8 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     for (int k = 0; k < 2; ++k) {
         d.pop[k] = b + L.off_pop[k];
         d.G[k] = (float4 *)(b + L.off_G[k]);
-        d.gmask[k] = (uint32_t *)(b + L.off_gmask[k]);
     }
-    d.umask = (uint32_t *)(b + L.off_umask);
+    d.amask = (uint32_t *)(b + L.off_amask);
     d.ufield = (float4 *)(b + L.off_ufield);
     d.status = (uint32_t *)(b + L.off_status);
     d.dropped = (double *)(b + L.off_dropped);
@@ -333,7 +351,7 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     LBIB_GUARD(s);
     if (tid != (int)s->topo.size()) return fail(s, LBIB_ERR_ID, "template ids must be consecutive from 0");
     if (!xyz || !tris) return fail(s, LBIB_ERR_ARG, "null mesh array");
-    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return fail(s, LBIB_ERR_ARG, "template node count must be in [4, 6144]");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return fail(s, LBIB_ERR_ARG, "template node count must be in [4, 5120]");
     Topology T;
     std::string err;
     if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return fail(s, LBIB_ERR_MESH, err);
@@ -358,17 +376,21 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     };
     std::vector<int32_t> tri4(4 * (size_t)nt), edge4(4 * (size_t)T.ne), quad4(4 * (size_t)T.ne);
     std::vector<float> ith0(T.ne);
-    for (int t = 0; t < nt; ++t) {
-        for (int k = 0; k < 3; ++k) tri4[4 * t + k] = T.tri[3 * t + k];
-        tri4[4 * t + 3] = fbits(T.S0[t]);
+    // device records in the conflict-free evaluation order of each kind
+    for (int j = 0; j < nt; ++j) {
+        const int t = T.tri_order[j];
+        for (int k = 0; k < 3; ++k) tri4[4 * j + k] = T.tri[3 * t + k];
+        tri4[4 * j + 3] = fbits(T.S0[t]);
     }
-    for (int e = 0; e < T.ne; ++e) {
-        edge4[4 * e] = T.edges[2 * e];
-        edge4[4 * e + 1] = T.edges[2 * e + 1];
-        edge4[4 * e + 2] = fbits(T.L0[e]);
-        edge4[4 * e + 3] = fbits(1.0 / T.L0[e]);
-        for (int k = 0; k < 4; ++k) quad4[4 * e + k] = T.quads[4 * e + k];
-        ith0[e] = (float)(1.0 / T.theta0[e]);
+    for (int j = 0; j < T.ne; ++j) {
+        const int e = T.edge_order[j];
+        edge4[4 * j] = T.edges[2 * e];
+        edge4[4 * j + 1] = T.edges[2 * e + 1];
+        edge4[4 * j + 2] = fbits(T.L0[e]);
+        edge4[4 * j + 3] = fbits(1.0 / T.L0[e]);
+        const int q = T.quad_order[j];
+        for (int k = 0; k < 4; ++k) quad4[4 * j + k] = T.quads[4 * q + k];
+        ith0[j] = (float)(1.0 / T.theta0[q]);
     }
     const size_t o_tri = put(tri4.data(), tri4.size() * 4);
     const size_t o_edge = put(edge4.data(), edge4.size() * 4);
@@ -433,7 +455,7 @@ lbib_status lbib_mesh_check(const double *xyz, int nn, const int32_t *tris, int 
         return code;
     };
     if (!xyz || !tris) return report(LBIB_ERR_ARG, "null mesh array");
-    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return report(LBIB_ERR_ARG, "node count must be in [4, 6144]");
+    if (nn < 4 || nn > MAX_TEMPLATE_NODES) return report(LBIB_ERR_ARG, "node count must be in [4, 5120]");
     Topology T;
     std::string err;
     if (!build_template(xyz, nn, tris, nt, stretch, T, err)) return report(LBIB_ERR_MESH, err);
@@ -524,6 +546,7 @@ lbib_status lbib_fluid_init(lbib_sim *s) {
     s->t = 0;
     s->gmode = -1;
     s->ufield_stale = false;
+    s->mark_stale = true;
     s->fluid_ready = true;
     return LBIB_OK;
 }
@@ -535,6 +558,8 @@ lbib_status lbib_step(lbib_sim *s, int n) {
     if (r != LBIB_OK) return r;
     for (int i = 0; i < n; ++i) {
         const int par = (int)(s->t & 1);
+        if (s->since_mark >= ACTIVE_RESET_STEPS) LBIB_CUDA(s, sim_remark(s, s->stream), "active cells");
+        s->since_mark++;
         cudaEvent_t *ev = nullptr;
         if (s->prof_on) {
             while (s->prof_ev.size() < s->prof_used + 3) {
@@ -645,8 +670,6 @@ lbib_status lbib_set_coupling_force(lbib_sim *s, const float *g, int64_t n) {
     float *tmp = nullptr;
     LBIB_CUDA(s, cudaMallocAsync((void **)&tmp, bytes, s->stream), "upload buffer");
     cudaError_t e = cudaMemcpyAsync(tmp, g, bytes, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync((char *)s->fluid_mem + L.off_gmask[gpar], 0, (size_t)L.nwords * 4, s->stream);
     if (e == cudaSuccess) e = launch_set_coupling(s->d, gpar, tmp, s->stream);
     cudaFreeAsync(tmp, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -691,14 +714,13 @@ lbib_status lbib_set_populations(lbib_sim *s, const double *h, int64_t n) {
     // the coupling-force history is not part of the populations
     FluidLayout L;
     fluid_layout(s->p, L);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
         e = cudaMemsetAsync((char *)s->fluid_mem + L.off_G[k], 0, (size_t)L.nf * 16, s->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync((char *)s->fluid_mem + L.off_gmask[k], 0, (size_t)L.nwords * 4, s->stream);
-    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "set populations");
     s->gmode = -2;
     s->ufield_stale = true;
+    s->mark_stale = true;
     return LBIB_OK;
 }
 

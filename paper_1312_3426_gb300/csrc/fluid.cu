@@ -81,7 +81,7 @@ __global__ void k_fields(SimDev s, int pop_par, int gmode, float *u, float *rho_
         Gy = s.gy;
         Gz = s.gz;
     }
-    if (gmode >= 0 && ((s.gmask[gmode][f >> 5] >> (f & 31)) & 1u)) {
+    if (gmode >= 0 && ((s.amask[f >> 5] >> (f & 31)) & 1u)) {
         const float4 g = s.G[gmode][f];
         Gx += g.x;
         Gy += g.y;
@@ -125,7 +125,7 @@ cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full
 __global__ void k_read_coupling(SimDev s, int gpar, float *g) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= s.nf) return;
-    if (!((s.gmask[gpar][f >> 5] >> (f & 31)) & 1u)) return;
+    if (!((s.amask[f >> 5] >> (f & 31)) & 1u)) return;
     const float4 v = s.G[gpar][f];
     const int64_t c = full_index(s, f);
     const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
@@ -146,7 +146,7 @@ __global__ void k_set_coupling(SimDev s, int gpar, const float *g) {
     const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
     const float4 v = make_float4(g[c], g[ncell + c], g[2 * ncell + c], 0.f);
     s.G[gpar][f] = v;
-    if (v.x != 0.f || v.y != 0.f || v.z != 0.f) atomicOr(s.gmask[gpar] + (f >> 5), 1u << (f & 31));
+    if (v.x != 0.f || v.y != 0.f || v.z != 0.f) atomicOr(s.amask + (f >> 5), 1u << (f & 31));
 }
 
 cudaError_t launch_set_coupling(const SimDev &s, int gpar, const float *g, cudaStream_t st) {

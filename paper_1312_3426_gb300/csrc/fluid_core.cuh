@@ -118,8 +118,7 @@ __device__ __forceinline__ void collide_store(T *__restrict__ dst, int nfp, int 
 }
 
 template <typename T>
-__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint32_t gcur, uint32_t gprv,
-                                           uint32_t um, int lane, uint32_t step_seed) {
+__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, bool active, uint32_t step_seed) {
     const T *__restrict__ src = (const T *)s.pop[par];
     T *__restrict__ dst = (T *)s.pop[par ^ 1];
     const int nfp = s.nfp;
@@ -137,15 +136,14 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint
     LBIB_PULL(14) LBIB_PULL(15) LBIB_PULL(16) LBIB_PULL(17) LBIB_PULL(18)
 #undef LBIB_PULL
 
-    const uint32_t bit = 1u << lane;
     float Gx = s.gx, Gy = s.gy, Gz = s.gz;
-    if (gcur & bit) {
+    if (active) {  // spread force of this step; clear the buffer of the next
         const float4 g = __ldcg(s.G[par] + f);
         Gx += g.x;
         Gy += g.y;
         Gz += g.z;
+        s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (gprv & bit) s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -169,7 +167,7 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, uint
     LBIB_COLL(14) LBIB_COLL(15) LBIB_COLL(16) LBIB_COLL(17) LBIB_COLL(18)
 #undef LBIB_COLL
 
-    if (um & bit) s.ufield[f] = make_float4(ux, uy, uz, rho);
+    if (active) s.ufield[f] = make_float4(ux, uy, uz, rho);
     if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
 }
 
@@ -182,25 +180,20 @@ __host__ __device__ __forceinline__ uint32_t step_seed(long long t) {
     return x;
 }
 
-// One block of FLUID_THREADS consecutive fluid cells starting at f0 (a
-// multiple of 32): every warp owns the mask words of its 32 cells, consumes
-// them and clears what this step used.
+// The active-cell word of the warp that owns fluid cell f (blocks start at
+// multiples of 32, so a warp owns exactly one word).  Read through L2: the
+// object update of the same launch may set bits.
+__device__ __forceinline__ uint32_t active_word(const SimDev &s, int f) {
+    const int w = f >> 5;
+    return (w < s.nwords) ? __ldcg(s.amask + w) : 0u;
+}
+
+// One block of FLUID_THREADS consecutive fluid cells starting at f0.
 template <typename T>
 __device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0, uint32_t step_seed) {
     const int f = f0 + (int)threadIdx.x;
-    const int w = f >> 5;
-    const int lane = threadIdx.x & 31;
-    uint32_t gcur = 0, gprv = 0, um = 0;
-    if (w < s.nwords) {  // L2 loads: in a batched launch other blocks set these bits
-        gcur = __ldcg(s.gmask[par] + w);
-        gprv = __ldcg(s.gmask[par ^ 1] + w);
-        um = __ldcg(s.umask + w);
-    }
-    if (f < s.nf) fluid_cell<T>(s, par, f, gcur, gprv, um, lane, step_seed);
-    if (lane == 0 && w < s.nwords) {
-        if (gprv) s.gmask[par ^ 1][w] = 0u;
-        if (um) s.umask[w] = 0u;
-    }
+    const uint32_t act = active_word(s, f);
+    if (f < s.nf) fluid_cell<T>(s, par, f, (act >> (threadIdx.x & 31)) & 1u, step_seed);
 }
 
 }  // namespace lbib

@@ -37,6 +37,23 @@ cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cuda
     return cudaLaunchKernelEx(&cfg, k_ib, s, par);
 }
 
+// Marks the cells around every node as active (after the mask was cleared).
+__global__ void k_mark_all(SimDev s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.nn_total) return;
+    const int NN = s.nn_total;
+    const df x{s.Xh[i], s.Xl[i]}, y{s.Xh[NN + i], s.Xl[NN + i]}, z{s.Xh[2 * NN + i], s.Xl[2 * NN + i]};
+    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) return;
+    const int3 c = lower_corner(x, y, z);
+    mark_halo(s, c.x, c.y, c.z);
+}
+
+cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st) {
+    if (s.nn_total == 0) return cudaSuccess;
+    k_mark_all<<<(s.nn_total + 255) / 256, 256, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
 // Object analysis (Sec. 5): mean position, bounds, volume, area, mean
 // velocity of one object, all in FP64 (a read-out, not part of the step).
 __global__ void k_analyze(SimDev s, int oid, double *out) {

@@ -30,10 +30,10 @@
 //      fixed order, interpolates the fluid velocity trilinearly from the 8
 //      surrounding lattice nodes (u = 0 on solid rows), applies the drag
 //      F_d = xi (u - v), spreads -F_d with the same weights (one 16-byte
-//      vector atomic per corner plus a bit in the live-entry mask) and
+//      vector atomic per corner) and
 //      advances v += (F + F_d + F_ext)/m, X += v (Eq. newton, unit time
-//      step); the 8 lattice nodes around the new position are marked so that
-//      the next fluid step writes their velocity.
+//      step); when the node's lower lattice corner changes, the 4x4x4 cells
+//      around the new position are marked active (see lbib_internal.h).
 // Node state is kept as hi + lo FP32 pairs (error-free two-sum arithmetic);
 // FP64 is used only for the per-object area and volume totals.
 #pragma once
@@ -84,16 +84,19 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 
 // Staged positions of one object: node q relative to the object's first
-// node is (hx[q] + lx[q], hy[q] + ly[q], hz[q] + lz[q]).
+// node is hi[q].xyz + lo[q].xyz (float4 for 16-byte shared-memory loads).
 struct Stage {
-    const float *hx, *hy, *hz, *lx, *ly, *lz;
+    const float4 *hi, *lo;
     // position of node q relative to node p; the difference of the hi parts
     // is exact for the nearby nodes of one element
     __device__ __forceinline__ f3 rel(int q, int p) const {
-        return {(hx[q] - hx[p]) + (lx[q] - lx[p]), (hy[q] - hy[p]) + (ly[q] - ly[p]),
-                (hz[q] - hz[p]) + (lz[q] - lz[p])};
+        const float4 a = hi[q], b = hi[p], c = lo[q], d = lo[p];
+        return {(a.x - b.x) + (c.x - d.x), (a.y - b.y) + (c.y - d.y), (a.z - b.z) + (c.z - d.z)};
     }
-    __device__ __forceinline__ f3 pos(int q) const { return {hx[q] + lx[q], hy[q] + ly[q], hz[q] + lz[q]}; }
+    __device__ __forceinline__ f3 pos(int q) const {
+        const float4 a = hi[q], c = lo[q];
+        return {a.x + c.x, a.y + c.y, a.z + c.z};
+    }
 };
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -162,11 +165,34 @@ __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corne
 
 __device__ __forceinline__ void mark(uint32_t *mask, int f) { atomicOr(mask + (f >> 5), 1u << (f & 31)); }
 
+// Marks the 4x4x4 lattice nodes (i0-1 .. i0+2, ...) around lower corner
+// (ix, iy, iz) as active.
+__device__ __forceinline__ void mark_halo(const SimDev &s, int ix, int iy, int iz) {
+    for (int dz = -1; dz <= 2; ++dz) {
+        const int cz = wrapi(iz + dz, s.nz);
+        for (int dy = -1; dy <= 2; ++dy)
+            for (int dx = -1; dx <= 2; ++dx) {
+                const int f = fluid_index(s, wrapi(ix + dx, s.nx), iy + dy, cz);
+                if (f >= 0) mark(s.amask, f);
+            }
+    }
+}
+
+// Lower lattice corner of a position.
+__device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
+    int3 c;
+    float w;
+    lattice_coord(x, c.x, w);
+    lattice_coord(y, c.y, w);
+    lattice_coord(z, c.z, w);
+    return c;
+}
+
 namespace cg = cooperative_groups;
 
-// Shared memory per block: 9 floats per node of the largest template (staged
-// position hi/lo, force) plus a small fixed tail.
-constexpr int IB_SMEM_PER_NODE = 9 * sizeof(float);
+// Shared memory per block: per node of the largest template the staged
+// position (two float4) and the force (3 floats), plus a small fixed tail.
+constexpr int IB_SMEM_PER_NODE = 11 * sizeof(float);
 constexpr int IB_SMEM_TAIL = 64;
 
 __host__ __device__ inline size_t ib_smem_bytes(int max_nodes) {
@@ -256,6 +282,7 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     df vx{Vh[i], Vl[i]}, vy{Vh[NN + i], Vl[NN + i]}, vz{Vh[2 * NN + i], Vl[2 * NN + i]};
     Corners c;
     corners(s, x, y, z, c);
+    const int3 c0 = lower_corner(x, y, z);
     float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -277,7 +304,6 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
         const float w = c.w[k];
         if (c.f[k] >= 0) {
             atomicAdd(G + c.f[k], make_float4(-w * fdx, -w * fdy, -w * fdz, 0.f));
-            mark(s.gmask[par], c.f[k]);
         } else {
             dropx -= w * fdx;
             dropy -= w * fdy;
@@ -311,15 +337,19 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) {
         atomicOr(s.status, ST_NODE_NAN);
     } else {
-        corners(s, x, y, z, c);
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (c.f[k] >= 0) mark(s.umask, c.f[k]);
+        const int3 lc = lower_corner(x, y, z);
+        if (lc.x != c0.x || lc.y != c0.y || lc.z != c0.z) mark_halo(s, lc.x, lc.y, lc.z);
     }
 }
 
 // Share [r n / C, (r+1) n / C) of n items for cluster rank r.
 __device__ __forceinline__ int share_lo(int n, int r, int C) { return (int)(((long long)n * r) / C); }
+
+// The same split on multiples of 32, so that a warp's 32 consecutive
+// elements are one group of the template's conflict-free order.
+__device__ __forceinline__ int share_lo32(int n, int r, int C) {
+    return r >= C ? n : (int)((((long long)n * r) / C) & ~31LL);
+}
 
 // The whole update of object o by the calling cluster (all C blocks call it).
 __device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int par, float *sh) {
@@ -329,21 +359,23 @@ __device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int pa
     const TplDev &T = s.tpl[ob.tid];
     const int nn = ob.nn, f0 = ob.first, NN = s.nn_total;
 
-    float *Fx = sh + 6 * nn, *Fy = sh + 7 * nn, *Fz = sh + 8 * nn;
-    float *tail = sh + 9 * nn;  // [0..3] this block's area / volume partials, [4..5] factors
-    const Stage P{sh, sh + nn, sh + 2 * nn, sh + 3 * nn, sh + 4 * nn, sh + 5 * nn};
+    float4 *hi = (float4 *)sh, *lo = hi + nn;
+    float *Fx = sh + 8 * nn, *Fy = sh + 9 * nn, *Fz = sh + 10 * nn;
+    float *tail = sh + 11 * nn;  // [0..3] this block's area / volume partials, [4..5] factors
+    const Stage P{hi, lo};
     const Forces F{Fx, Fy, Fz};
 
     // 1. stage positions relative to the first node, clear the forces
     for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+        df d[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const df a{s.Xh[k * NN + f0 + p], s.Xl[k * NN + f0 + p]};
             const df b{s.Xh[k * NN + f0], s.Xl[k * NN + f0]};
-            const df d = df_add(a, {-b.hi, -b.lo});
-            sh[k * nn + p] = d.hi;
-            sh[(3 + k) * nn + p] = d.lo;
+            d[k] = df_add(a, {-b.hi, -b.lo});
         }
+        hi[p] = make_float4(d[0].hi, d[1].hi, d[2].hi, 0.f);
+        lo[p] = make_float4(d[0].lo, d[1].lo, d[2].lo, 0.f);
         Fx[p] = 0.f;
         Fy[p] = 0.f;
         Fz[p] = 0.f;
@@ -392,18 +424,23 @@ __device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int pa
     __syncthreads();
     const float dSg = tail[4], dV = tail[5];
 
-    // 3. this block's share of the elements [edges | pairs | triangles]
-    const int ne = (T.ks != 0.f) ? T.ne : 0;
-    const int nq = (T.kb != 0.f) ? T.ne : 0;
-    const int nt = (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) ? T.nt : 0;
-    const int M = ne + nq + nt;
-    for (int k = share_lo(M, r, C) + threadIdx.x; k < share_lo(M, r + 1, C); k += blockDim.x) {
-        if (k < ne)
-            edge_force(T, P, k, F);
-        else if (k < ne + nq)
-            bending_force(T, P, k - ne, F);
-        else
-            triangle_force(T, P, k - ne - nq, dSg, dV, F);
+    // 3. this block's share of each kind of element; one loop per kind so
+    //    that independent iterations overlap
+    if (T.ks != 0.f) {
+        const int e1 = share_lo32(T.ne, r + 1, C);
+#pragma unroll 2
+        for (int e = share_lo32(T.ne, r, C) + threadIdx.x; e < e1; e += blockDim.x) edge_force(T, P, e, F);
+    }
+    if (T.kb != 0.f) {
+        const int e1 = share_lo32(T.ne, r + 1, C);
+#pragma unroll 2
+        for (int e = share_lo32(T.ne, r, C) + threadIdx.x; e < e1; e += blockDim.x) bending_force(T, P, e, F);
+    }
+    if (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) {
+        const int t1 = share_lo32(T.nt, r + 1, C);
+#pragma unroll 2
+        for (int t = share_lo32(T.nt, r, C) + threadIdx.x; t < t1; t += blockDim.x)
+            triangle_force(T, P, t, dSg, dV, F);
     }
     cl.sync();  // every block's partial forces complete
 
@@ -412,7 +449,7 @@ __device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int pa
     for (int p = share_lo(nn, r, C) + threadIdx.x; p < share_lo(nn, r + 1, C); p += blockDim.x) {
         f3 Fp = mk(0.f, 0.f, 0.f);
         for (int j = 0; j < C; ++j) {
-            const float *Fj = cl.map_shared_rank(sh, j) + 6 * nn;
+            const float *Fj = cl.map_shared_rank(sh, j) + 8 * nn;
             Fp = Fp + mk(Fj[p], Fj[nn + p], Fj[2 * nn + p]);
         }
         node_update(s, o, f0 + p, Fp, ob.inv_mass, par);

@@ -8,15 +8,21 @@
 //                    (plane stride nfp = nf rounded up to 64 elements), the
 //                    deviation h_i = f_i - w_i rho0 (times 2^s for FP16/BF16).
 //                    Step t pulls from pop[t&1] and writes pop[(t+1)&1].
-//   coupling force   G[2][nf] float4, dense but touched only where nodes
-//                    spread; bit f of gmask[2][nwords] marks a live entry.
-//                    Step t spreads into G[t&1]; the fluid step t consumes
-//                    G[t&1] and clears G[(t+1)&1] (consumed one step before),
-//                    so after step t the buffer of step t is still readable.
-//   velocity samples ufield[nf] float4 (u, rho) written by the fluid step
-//                    only at cells whose bit is set in umask: the 8 lattice
-//                    nodes around every node position, marked by the node
-//                    update of the same step and read by the next one.
+//   active cells     bit f of amask[nwords] marks the cells near objects: the
+//                    4x4x4 lattice nodes around every node (its 8
+//                    interpolation corners and a one-cell halo).  A node
+//                    marks them when its lower corner changes; marks persist
+//                    until a periodic reset, after which all nodes re-mark.
+//                    Nodes move less than one cell per step, so a node's
+//                    corners at the next step are always active already.
+//   coupling force   G[2][nf] float4, dense, non-zero only at active cells.
+//                    Step t spreads into G[t&1]; the fluid step t adds
+//                    G[t&1] at active cells and zeroes G[(t+1)&1] there (the
+//                    buffer step t+1 spreads into), so after step t the
+//                    buffer of step t is still readable.
+//   velocity samples ufield[nf] float4 (u, rho) written by the fluid step at
+//                    active cells and read at the node corners by the next
+//                    step.
 //   nodes            positions and velocities as unevaluated sums of two
 //                    FP32 numbers (hi + lo, about 48 significant bits):
 //                    Xh, Xl, Vh, Vl each [3][nn_total], structure of arrays,
@@ -33,7 +39,8 @@ namespace lbib {
 constexpr int NQ = 19;
 constexpr int FLUID_THREADS = 256;
 constexpr int IB_THREADS = 256;
-constexpr int MAX_TEMPLATE_NODES = 6144;  // 9 floats of shared memory per node
+constexpr int MAX_TEMPLATE_NODES = 5120;  // 11 floats of shared memory per node
+constexpr int ACTIVE_RESET_STEPS = 128;    // period of the active-cell re-marking
 
 // D3Q19 directions of this library: rest, the 6 axis directions in +/- pairs,
 // then the 12 face diagonals in +/- pairs; opposite(q) = q+1 for odd q,
@@ -96,8 +103,7 @@ struct SimDev {
     float xi;
     void *pop[2];
     float4 *G[2];
-    uint32_t *gmask[2];
-    uint32_t *umask;
+    uint32_t *amask;
     float4 *ufield;
     float *Xh, *Xl, *Vh, *Vl; // [3][nn_total] each
     int nn_total, nobj;
@@ -122,6 +128,7 @@ cudaError_t launch_mass(const SimDev &s, int pop_par, double *acc, cudaStream_t 
 // one cluster of `cluster` blocks per object; max_nodes sizes shared memory
 cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cudaStream_t st);
 // oid >= 0: one object into out[14]; oid < 0: every object into out[nobj][14]
+cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st);
 cudaError_t launch_analyze(const SimDev &s, int oid, double *out, cudaStream_t st);
 
 }  // namespace lbib

@@ -55,6 +55,8 @@ struct lbib_sim {
     int64_t t = 0;               // steps since lbib_fluid_init (buffer parity)
     int gmode = -1;              // force applied by the collision that produced the current populations
     bool ufield_stale = false;   // velocity samples must be recomputed before the next step
+    bool mark_stale = true;      // the active-cell mask must be rebuilt before the next step
+    int since_mark = 0;          // steps since the active-cell mask was rebuilt
 };
 
 namespace lbib {
@@ -62,4 +64,5 @@ lbib_status sim_check_status(lbib_sim *s);
 lbib_status sim_download_nodes(lbib_sim *s);
 lbib_status sim_upload(lbib_sim *s);
 lbib_status sim_prepare_step(lbib_sim *s);
+cudaError_t sim_remark(lbib_sim *s, cudaStream_t st);
 }  // namespace lbib

@@ -159,7 +159,39 @@ bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, cons
         return false;
     }
 
+    T.edge_order = conflict_free_order(T.edges, 2, 32);
+    T.quad_order = conflict_free_order(T.quads, 4, 32);
+    T.tri_order = conflict_free_order(T.tri, 3, 32);
     return true;
+}
+
+std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width) {
+    const int n = (int)(nodes.size() / arity);
+    int max_node = 0;
+    for (int v : nodes) max_node = std::max(max_node, v);
+    std::vector<int> stamp(max_node + 1, -1), order, rest;
+    std::vector<int> remaining(n);
+    for (int i = 0; i < n; ++i) remaining[i] = i;
+    order.reserve(n);
+    int group = 0;
+    while (!remaining.empty()) {
+        rest.clear();
+        int filled = 0;
+        for (int e : remaining) {
+            bool free = filled < width;
+            for (int k = 0; k < arity && free; ++k) free = stamp[nodes[arity * e + k]] != group;
+            if (free) {
+                for (int k = 0; k < arity; ++k) stamp[nodes[arity * e + k]] = group;
+                order.push_back(e);
+                ++filled;
+            } else {
+                rest.push_back(e);
+            }
+        }
+        remaining.swap(rest);
+        ++group;
+    }
+    return order;
 }
 
 }  // namespace lbib

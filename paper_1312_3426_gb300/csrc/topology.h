@@ -16,7 +16,15 @@ struct Topology {
     std::vector<int> quads;                   // [ne][4] (a, b, c, d)
     std::vector<double> L0, theta0, S0;       // [ne], [ne], [nt]
     double Sg0 = 0.0, V0 = 0.0;
+    // device evaluation order of each element list: consecutive groups of 32
+    // elements touch pairwise-different nodes where possible, so the lanes of
+    // a warp add to different nodes' force sums
+    std::vector<int> edge_order, quad_order, tri_order;
 };
+
+// Greedy packing of elements (node lists of `arity` ids each) into groups of
+// `width` with disjoint nodes; returns the evaluation order.
+std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width);
 
 bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
                     Topology &out, std::string &err);
