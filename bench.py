@@ -55,6 +55,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ib-cluster", type=int, default=0, help="thread blocks per object (0: library default)")
+    ap.add_argument("--overlap", type=int, default=-1, choices=(-1, 0, 1),
+                    help="membrane forces overlapped with the fluid step (-1: library default)")
+    ap.add_argument("--membrane-clusters", type=int, default=-1,
+                    help="clusters of the membrane kernel (0: one per object, -1: library default)")
     ap.add_argument("--launch", choices=["separate", "persistent"], default="separate",
                     help="one launch per phase (lbib_step) or one persistent launch per step (lbib_batch_step)")
     return ap.parse_args()
@@ -229,6 +233,10 @@ def main():
     nf = sc.n_fluid_cells
     if args.ib_cluster:
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
+    if args.overlap >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
+    if args.membrane_clusters >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
     sim.step(max(3, args.warmup))
     sim.sync()
 
@@ -264,10 +272,11 @@ def main():
 
     if prof is not None:
         fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
-        ib_ms = prof["ib_ms"] / max(1, prof["ib_launches"])
+        nodes_ms = prof["nodes_ms"] / max(1, prof["nodes_launches"])
+        membrane_ms = prof["membrane_ms"] / max(1, prof["membrane_launches"])
     else:  # one fused launch per step: the whole step is the kernel
         fluid_ms = ms / args.steps
-        ib_ms = 0.0
+        nodes_ms = membrane_ms = 0.0
     peak, peak_kind = measured_peak()
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * nf / (fluid_ms / 1e3) / 1e9
@@ -316,10 +325,14 @@ def main():
                          "kernel": "k_batch_step" if persistent else f"k_fluid<{args.precision}>",
                          "bytes_per_cell": bpc,
                          "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
-            "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "ib": round(ib_ms, 5)},
+            "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "nodes": round(nodes_ms, 5),
+                                  "membrane_overlapped": round(membrane_ms, 5)},
             "nodes_per_s": round(world * sc.n_nodes * args.steps / (ms / 1e3), 1),
             "step_hbm_frac": round((bpc * nf + 400 * sc.n_nodes) / (ms / args.steps / 1e3) / 1e9 / peak, 4),
-            "gpu_launches": args.steps * (1 if persistent else (2 if sc.objects else 1)),
+            # per step: fluid, node update and (second stream) membrane
+            # kernels; the active-cell mask is rebuilt every 128 steps
+            "gpu_launches": args.steps * (1 if persistent else (3 if sc.objects else 1))
+            + (args.steps // 128 if sc.objects else 0),
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": base,

@@ -29,7 +29,11 @@
  *     lbib_destroy.
  *   - Work is enqueued on the CUDA stream given to lbib_create (0 = legacy
  *     default stream).  lbib_step returns before the GPU finishes; read-outs
- *     and lbib_sync wait for it.
+ *     and lbib_sync wait for it.  Inside lbib_step the membrane forces of
+ *     the next step are computed on a second, library-owned stream while
+ *     the fluid step runs; lbib_step orders that stream behind the given
+ *     one with CUDA events and makes the given stream wait for it before
+ *     returning, so later work on the given stream sees a finished step.
  *   - The library uses the current CUDA device at lbib_create for all later
  *     calls on that simulation.
  */
@@ -158,8 +162,10 @@ LBIB_API lbib_status lbib_fluid_init(lbib_sim *sim);
 /* Advances n_steps full steps (Eq. lbequation, Eq. newton, Eq. dragforce,
  * Sec. 4): object measures and membrane forces, interpolation, drag,
  * spreading and node update, then fluid stream + collide with the body
- * force plus the spread force.  Asynchronous on the simulation's stream;
- * device-side errors surface at the next synchronising call. */
+ * force plus the spread force.  The membrane forces of step t+1 depend on
+ * the node positions only and are computed while the fluid part of step t
+ * runs.  Asynchronous on the simulation's stream; device-side errors
+ * surface at the next synchronising call. */
 LBIB_API lbib_status lbib_step(lbib_sim *sim, int n_steps);
 
 /* Waits for the simulation's stream and returns the sticky device status. */
@@ -207,13 +213,15 @@ LBIB_API lbib_status lbib_object_analyze(lbib_sim *sim, int oid, double out[14])
 LBIB_API lbib_status lbib_objects_set_force(lbib_sim *sim, const double *f, int n_obj);
 LBIB_API lbib_status lbib_objects_analyze(lbib_sim *sim, double *out, int64_t cap);
 
-/* Per-phase timing with CUDA events on the simulation's stream.  While
- * enabled, lbib_step records events around each kernel of each step.
- * lbib_profile_read waits for the stream and returns, since the last
+/* Per-phase timing with CUDA events on the streams the kernels run on.
+ * While enabled, lbib_step records events around each kernel of each step.
+ * lbib_profile_read waits for both streams and returns, since the last
  * enable: out[0] total ms and out[1] launches of the fluid kernel, out[2]
- * total ms and out[3] launches of the object kernel. */
+ * total ms and out[3] launches of the node-update kernel, out[4] total ms
+ * and out[5] launches of the membrane-force kernel (which overlaps the
+ * fluid kernel). */
 LBIB_API lbib_status lbib_profile_enable(lbib_sim *sim, int on);
-LBIB_API lbib_status lbib_profile_read(lbib_sim *sim, double out[4]);
+LBIB_API lbib_status lbib_profile_read(lbib_sim *sim, double out[6]);
 
 /* Total fluid mass sum_cells sum_i f_i, an FP64 reduction on the GPU. */
 LBIB_API lbib_status lbib_fluid_mass(lbib_sim *sim, double *mass);
@@ -241,11 +249,17 @@ LBIB_API int64_t lbib_footprint_bytes(const lbib_fluid_params *params, int64_t n
 LBIB_API lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps);
 
 /* Launch-shape knobs, chosen by the autotuner of the Python package or set
- * by hand.  LBIB_TUNE_IB_CLUSTER: thread blocks per object in the object
- * kernel (1..8, default 4).  Results do not depend on the knobs beyond the
- * order of floating-point atomics.  LBIB_ERR_ARG for an unknown key or an
- * out-of-range value. */
-typedef enum { LBIB_TUNE_IB_CLUSTER = 0 } lbib_tune_key;
+ * by hand.  LBIB_TUNE_IB_CLUSTER: thread blocks per object in the
+ * membrane-force kernel (1..8, default 1).  LBIB_TUNE_OVERLAP: 1 (default)
+ * computes the membrane forces of step t+1 on the library's second stream
+ * while the fluid part of step t runs; 0 computes them on the simulation's
+ * stream at the start of each step.  LBIB_TUNE_MEMBRANE_CLUSTERS: number of
+ * clusters of the membrane-force kernel, each looping over the objects
+ * (0, default: one cluster per object; a small grid leaves most SMs to the
+ * fluid kernel running beside it).  Results do not depend on the knobs
+ * beyond the order of floating-point atomics.  LBIB_ERR_ARG for an unknown
+ * key or an out-of-range value. */
+typedef enum { LBIB_TUNE_IB_CLUSTER = 0, LBIB_TUNE_OVERLAP = 1, LBIB_TUNE_MEMBRANE_CLUSTERS = 2 } lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);
 

@@ -4,7 +4,8 @@
 // The grid is made of thread-block clusters (as many as fit on the GPU at
 // once).  Phase A: each cluster takes objects, of any simulation, from an
 // atomic ticket (rank 0 draws it and the cluster reads it through
-// distributed shared memory) and updates them as in ib_core.cuh.  Phase B:
+// distributed shared memory) and updates them as in ib_core.cuh (membrane
+// part, then the coupling part of the object's nodes by the same cluster).  Phase B:
 // once the objects are handed out, every block takes blocks of
 // FLUID_THREADS fluid cells, of any simulation, from a second ticket.  A warp
 // whose 32 cells include active cells (cells near objects, see
@@ -54,9 +55,17 @@ __global__ void __launch_bounds__(FLUID_THREADS) k_batch_step(const SimDev *__re
         cl.sync();  // every block has read the ticket before rank 0 draws again
         if (k >= n_ib) break;
         const int2 it = ib_items[k];
-        const SimDev s = sims[it.x];
+        const SimDev &s = sims[it.x];
         const int par = (par_base[it.x] + step_off) & 1;
-        ib_cluster_object(s, it.y, par, batch_smem);
+        membrane_object(s, it.y, batch_smem);
+        // the object's nodes: coupling and update (membrane forces visible
+        // after the cluster barrier that ends membrane_object)
+        {
+            const ObjDev ob = s.obj[it.y];
+            const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+            for (int p = share_lo(ob.nn, r, C) + threadIdx.x; p < share_lo(ob.nn, r + 1, C); p += blockDim.x)
+                node_step(s, ob.first + p, par);
+        }
         __syncthreads();
         if (threadIdx.x == 0) __threadfence();  // this block's node updates, device-wide
         cl.sync();
@@ -69,7 +78,7 @@ __global__ void __launch_bounds__(FLUID_THREADS) k_batch_step(const SimDev *__re
         __syncthreads();
         if (k >= n_fl) break;
         const int2 it = fl_items[k];
-        const SimDev s = sims[it.x];
+        const SimDev &s = sims[it.x];
         const int par = (par_base[it.x] + step_off) & 1;
         const int f = it.y * FLUID_THREADS + (int)threadIdx.x;
         const uint32_t act = active_word(s, f);  // warp-uniform
@@ -290,7 +299,10 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
             s->gmode = (int)(s->t & 1);
             s->t++;
         }
-        if (n_steps > 0 && s->nn_total > 0) s->dev_newer = true;
+        if (n_steps > 0 && s->nn_total > 0) {
+            s->dev_newer = true;
+            s->fel_valid = false;  // membrane forces are those of the last step, not the next
+        }
     }
     return LBIB_OK;
 }

@@ -165,6 +165,7 @@ lbib_status sim_upload(lbib_sim *s) {
         s->d.fext = s->d_fext;
         s->d.nobj = nobj;
         s->tables_dirty = false;
+        s->fel_valid = false;
     }
     if (s->fext_dirty && !s->objs.empty()) {
         LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext.data(), s->fext.size() * sizeof(float),
@@ -178,12 +179,13 @@ lbib_status sim_upload(lbib_sim *s) {
             if (s->dnodes) cudaFree(s->dnodes);
             s->dnodes = nullptr;
             s->node_bytes = 0;
-            LBIB_CUDA(s, cudaMalloc(&s->dnodes, 12 * (size_t)nn * 4), "node state");
+            LBIB_CUDA(s, cudaMalloc(&s->dnodes, 16 * (size_t)nn * 4), "node state");
             s->dev_nn_cap = nn;
-            s->node_bytes = 12 * (size_t)nn * 4;
+            s->node_bytes = 16 * (size_t)nn * 4;
         }
-        // FP64 host values split exactly into hi + lo FP32 pairs (48 bits)
-        std::vector<float> st(12 * (size_t)nn);
+        // FP64 host values split exactly into hi + lo FP32 pairs (48 bits);
+        // the membrane forces are recomputed before they are used
+        std::vector<float> st(16 * (size_t)nn, 0.f);
         const size_t n3 = 3 * (size_t)nn;
         for (int i = 0; i < nn; ++i)
             for (int k = 0; k < 3; ++k) {
@@ -194,14 +196,20 @@ lbib_status sim_upload(lbib_sim *s) {
                 st[2 * n3 + j] = (float)v;
                 st[3 * n3 + j] = (float)(v - (double)st[2 * n3 + j]);
             }
+        int32_t *owner = (int32_t *)(st.data() + 5 * n3);
+        for (int o = 0; o < (int)s->objs.size(); ++o)
+            for (int p = 0; p < s->objs[o].nn; ++p) owner[s->objs[o].first + p] = o;
         LBIB_CUDA(s, cudaMemcpyAsync(s->dnodes, st.data(), st.size() * 4, cudaMemcpyHostToDevice, s->stream), "nodes H2D");
         LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "nodes H2D");
         s->d.Xh = s->dnodes;
         s->d.Xl = s->dnodes + n3;
         s->d.Vh = s->dnodes + 2 * n3;
         s->d.Vl = s->dnodes + 3 * n3;
+        s->d.Fel = s->dnodes + 4 * n3;
+        s->d.node_obj = (const int *)(s->dnodes + 5 * n3);
         s->d.nn_total = nn;
         s->host_newer = false;
+        s->fel_valid = false;
         // the velocity samples must be valid at the (new) node corners, and
         // the active cells must follow the nodes
         if (!(s->t == 0 && s->gmode == -1)) s->ufield_stale = true;
@@ -261,8 +269,9 @@ int64_t lbib_footprint_bytes(const lbib_fluid_params *p, int64_t n_nodes, int64_
     if (!p) return -1;
     FluidLayout L;
     if (!fluid_layout(*p, L)) return -1;
-    // nodes: X, V (FP64); templates: ~ 3 edge + 12 bending + 3 triangle records per node
-    return (int64_t)L.total + n_nodes * 48 + n_tri_total * (16 + 3 * 16 + 4 * 20);
+    // nodes: X, V (hi + lo FP32), membrane force, owner; templates: triangle,
+    // edge and bending records
+    return (int64_t)L.total + n_nodes * 64 + n_tri_total * (16 + 3 * 16 + 4 * 20);
 }
 
 lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out) {
@@ -318,7 +327,16 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     d.dropped = (double *)(b + L.off_dropped);
     e = cudaMemsetAsync(s->fluid_mem, 0, L.total, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    // the membrane kernel is short and on the critical path only if it
+    // finishes after the fluid kernel: its blocks go first
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, prio_greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_nodes, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_membrane, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (s->ev_nodes) cudaEventDestroy(s->ev_nodes);
+        if (s->aux) cudaStreamDestroy(s->aux);
         cudaFree(s->fluid_mem);
         delete s;
         return LBIB_ERR_CUDA;
@@ -331,6 +349,12 @@ void lbib_destroy(lbib_sim *s) {
     if (!s) return;
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->stream);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+    }
+    if (s->ev_nodes) cudaEventDestroy(s->ev_nodes);
+    if (s->ev_membrane) cudaEventDestroy(s->ev_membrane);
     for (auto &t : s->tpl_mem) cudaFree(t);
     if (s->d_tpl) cudaFree(s->d_tpl);
     if (s->d_obj) cudaFree(s->d_obj);
@@ -338,6 +362,7 @@ void lbib_destroy(lbib_sim *s) {
     if (s->d_analyze) cudaFree(s->d_analyze);
 
     for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->prof_aux) cudaEventDestroy(e);
     if (s->dnodes) cudaFree(s->dnodes);
     if (s->fluid_mem) cudaFree(s->fluid_mem);
     delete s;
@@ -551,33 +576,80 @@ lbib_status lbib_fluid_init(lbib_sim *s) {
     return LBIB_OK;
 }
 
+// Profiling events: `k` more from pool `pool`, created on demand.
+static lbib_status prof_events(lbib_sim *s, std::vector<cudaEvent_t> &pool, size_t &used, int k, cudaEvent_t **ev) {
+    while (pool.size() < used + k) {
+        cudaEvent_t e;
+        LBIB_CUDA(s, cudaEventCreate(&e), "profile event");
+        pool.push_back(e);
+    }
+    *ev = &pool[used];
+    used += k;
+    return LBIB_OK;
+}
+
+// Membrane forces of the current node positions, on stream `st`.
+static lbib_status launch_membrane_timed(lbib_sim *s, cudaStream_t st) {
+    cudaEvent_t *ev = nullptr;
+    if (s->prof_on) {
+        lbib_status r = prof_events(s, s->prof_aux, s->prof_aux_used, 2, &ev);
+        if (r != LBIB_OK) return r;
+        LBIB_CUDA(s, cudaEventRecord(ev[0], st), "profile event");
+    }
+    LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, st), "membrane forces");
+    if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], st), "profile event");
+    return LBIB_OK;
+}
+
+// One step is: coupling part of the object update (node kernel), then the
+// fluid step; the membrane part of the NEXT step depends only on the node
+// positions the node kernel wrote, so (overlap on) it runs on the second
+// stream while the fluid step runs:
+//   stream: [membrane(t) if not ready] nodes(t) -> ev_nodes, fluid(t), wait ev_membrane
+//   aux:    wait ev_nodes, membrane(t+1) -> ev_membrane
+// and `stream` has caught up with `aux` when the call returns.  With overlap
+// off every step is membrane(t), nodes(t), fluid(t) on `stream`.
 lbib_status lbib_step(lbib_sim *s, int n) {
     LBIB_GUARD(s);
     if (n < 0) return fail(s, LBIB_ERR_ARG, "negative step count");
     lbib_status r = sim_prepare_step(s);
     if (r != LBIB_OK) return r;
+    const bool objects = s->nn_total > 0 && !s->objs.empty();
+    if (n > 0 && objects && !s->fel_valid && s->overlap) {
+        r = launch_membrane_timed(s, s->stream);
+        if (r != LBIB_OK) return r;
+        s->fel_valid = true;
+    }
     for (int i = 0; i < n; ++i) {
         const int par = (int)(s->t & 1);
         if (s->since_mark >= ACTIVE_RESET_STEPS) LBIB_CUDA(s, sim_remark(s, s->stream), "active cells");
         s->since_mark++;
+        if (objects && !s->overlap) {
+            r = launch_membrane_timed(s, s->stream);
+            if (r != LBIB_OK) return r;
+        }
         cudaEvent_t *ev = nullptr;
         if (s->prof_on) {
-            while (s->prof_ev.size() < s->prof_used + 3) {
-                cudaEvent_t e;
-                LBIB_CUDA(s, cudaEventCreate(&e), "profile event");
-                s->prof_ev.push_back(e);
-            }
-            ev = &s->prof_ev[s->prof_used];
-            s->prof_used += 3;
+            r = prof_events(s, s->prof_ev, s->prof_used, 3, &ev);
+            if (r != LBIB_OK) return r;
             LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
         }
-        LBIB_CUDA(s, launch_ib(s->d, par, s->max_nodes, s->cluster, s->stream), "ib step");
+        if (objects) LBIB_CUDA(s, launch_nodes(s->d, par, s->stream), "node update");
+        if (objects && s->overlap) {
+            LBIB_CUDA(s, cudaEventRecord(s->ev_nodes, s->stream), "event");
+            LBIB_CUDA(s, cudaStreamWaitEvent(s->aux, s->ev_nodes, 0), "event");
+            r = launch_membrane_timed(s, s->aux);
+            if (r != LBIB_OK) return r;
+            LBIB_CUDA(s, cudaEventRecord(s->ev_membrane, s->aux), "event");
+        }
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], s->stream), "profile event");
         LBIB_CUDA(s, launch_fluid(s->d, par, (long long)s->t, s->stream), "fluid step");
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[2], s->stream), "profile event");
+        if (objects && s->overlap) LBIB_CUDA(s, cudaStreamWaitEvent(s->stream, s->ev_membrane, 0), "event");
         s->t++;
         s->gmode = par;
     }
+    if (!s->overlap) s->fel_valid = false;
     if (n > 0 && s->nn_total > 0) s->dev_newer = true;
     return LBIB_OK;
 }
@@ -807,6 +879,16 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         s->cluster = value;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_OVERLAP) {
+        if (value != 0 && value != 1) return fail(s, LBIB_ERR_ARG, "overlap must be 0 or 1");
+        s->overlap = value != 0;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_MEMBRANE_CLUSTERS) {
+        if (value < 0 || value > (1 << 20)) return fail(s, LBIB_ERR_ARG, "membrane clusters must be in [0, 2^20]");
+        s->membrane_clusters = value;
+        return LBIB_OK;
+    }
     return fail(s, LBIB_ERR_ARG, "unknown tuning key");
 }
 
@@ -816,6 +898,14 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
         *value = s->cluster;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_OVERLAP) {
+        *value = s->overlap ? 1 : 0;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_MEMBRANE_CLUSTERS) {
+        *value = s->membrane_clusters;
+        return LBIB_OK;
+    }
     return LBIB_ERR_ARG;
 }
 
@@ -823,26 +913,35 @@ lbib_status lbib_profile_enable(lbib_sim *s, int on) {
     LBIB_GUARD(s);
     s->prof_on = on != 0;
     s->prof_used = 0;
+    s->prof_aux_used = 0;
     return LBIB_OK;
 }
 
-lbib_status lbib_profile_read(lbib_sim *s, double out[4]) {
+lbib_status lbib_profile_read(lbib_sim *s, double out[6]) {
     LBIB_GUARD(s);
     if (!out) return fail(s, LBIB_ERR_ARG, "null output");
     LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "profile");
-    double fl = 0.0, ib = 0.0;
+    LBIB_CUDA(s, cudaStreamSynchronize(s->aux), "profile");
+    double fl = 0.0, nodes = 0.0, mem = 0.0;
     for (size_t k = 0; k + 3 <= s->prof_used; k += 3) {
         float a = 0.f, b = 0.f;
         LBIB_CUDA(s, cudaEventElapsedTime(&a, s->prof_ev[k], s->prof_ev[k + 1]), "profile");
         LBIB_CUDA(s, cudaEventElapsedTime(&b, s->prof_ev[k + 1], s->prof_ev[k + 2]), "profile");
-        ib += a;
+        nodes += a;
         fl += b;
+    }
+    for (size_t k = 0; k + 2 <= s->prof_aux_used; k += 2) {
+        float a = 0.f;
+        LBIB_CUDA(s, cudaEventElapsedTime(&a, s->prof_aux[k], s->prof_aux[k + 1]), "profile");
+        mem += a;
     }
     const double steps = (double)(s->prof_used / 3);
     out[0] = fl;
     out[1] = steps;
-    out[2] = ib;
+    out[2] = nodes;
     out[3] = s->objs.empty() ? 0.0 : steps;
+    out[4] = mem;
+    out[5] = (double)(s->prof_aux_used / 2);
     return LBIB_OK;
 }
 

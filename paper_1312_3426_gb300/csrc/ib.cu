@@ -1,29 +1,40 @@
-// Immersed-boundary kernel of one simulation: one thread-block cluster per
-// object, as described in ib_core.cuh.
+// Immersed-boundary kernels of one simulation: the membrane part (one
+// thread-block cluster per object) and the coupling part (one thread per
+// node), as described in ib_core.cuh.
 #include "ib_core.cuh"
 
 namespace lbib {
 
 extern __shared__ float ib_smem[];
 
-__global__ void __launch_bounds__(IB_THREADS, 4) k_ib(SimDev s, int par) {
+// Cluster c takes objects c, c + n_clusters, ... (a grid smaller than the
+// object count leaves SMs to the fluid kernel that runs beside it).
+__global__ void __launch_bounds__(IB_THREADS, 4) k_membrane(SimDev s) {
     cg::cluster_group cl = cg::this_cluster();
-    ib_cluster_object(s, (int)(blockIdx.x / cl.num_blocks()), par, ib_smem);
+    const int C = (int)cl.num_blocks();
+    const int n_clusters = (int)(gridDim.x / C);
+    for (int o = (int)(blockIdx.x / C); o < s.nobj; o += n_clusters) membrane_object(s, o, ib_smem);
 }
 
-cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cudaStream_t st) {
+__global__ void __launch_bounds__(IB_THREADS, 4) k_nodes(SimDev s, int par) {
+    const int i = blockIdx.x * IB_THREADS + threadIdx.x;
+    if (i < s.nn_total) node_step(s, i, par);
+}
+
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, cudaStream_t st) {
     if (s.nobj == 0) return cudaSuccess;
     const size_t smem = ib_smem_bytes(max_nodes);
     static size_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_ib, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_ib, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_membrane, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(s.nobj * cluster));
+    const int n_clusters = (max_clusters > 0 && max_clusters < s.nobj) ? max_clusters : s.nobj;
+    cfg.gridDim = dim3((unsigned)(n_clusters * cluster));
     cfg.blockDim = dim3(IB_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -34,7 +45,13 @@ cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cuda
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ib, s, par);
+    return cudaLaunchKernelEx(&cfg, k_membrane, s);
+}
+
+cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st) {
+    if (s.nn_total == 0) return cudaSuccess;
+    k_nodes<<<(s.nn_total + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, st>>>(s, par);
+    return cudaGetLastError();
 }
 
 // Marks the cells around every node as active (after the mask was cleared).

@@ -1,8 +1,10 @@
-// Device-side body of the immersed-boundary update (Sec. 2 and Sec. 4 of
-// arXiv:1312.3426), shared by the single-simulation kernel (ib.cu) and the
-// batched persistent kernel (batch.cu).
+// Device-side bodies of the immersed-boundary update (Sec. 2 and Sec. 4 of
+// arXiv:1312.3426), shared by the single-simulation kernels (ib.cu) and the
+// batched persistent kernel (batch.cu).  The update has two parts.
 //
-// One thread-block cluster of C blocks updates one object:
+// Membrane part, one thread-block cluster of C blocks per object; it needs
+// only the node positions, so it can run while the fluid step that precedes
+// it is still in progress:
 //   1. every block stages the positions of all the object's nodes, relative
 //      to its first node, as hi + lo FP32 pairs in shared memory, and clears
 //      its own force array;
@@ -25,15 +27,16 @@
 //                   centroid to vertex v, and volume kv (V-V0)/V0 S n_in / 3;
 //      a pair of opposite contributions is the same FP32 value with both
 //      signs, so internal forces cancel up to the rounding of the sums;
-//   4. after a cluster barrier every block takes its share of the nodes, sums
-//      the C partial force arrays through distributed shared memory in a
-//      fixed order, interpolates the fluid velocity trilinearly from the 8
-//      surrounding lattice nodes (u = 0 on solid rows), applies the drag
-//      F_d = xi (u - v), spreads -F_d with the same weights (one 16-byte
-//      vector atomic per corner) and
-//      advances v += (F + F_d + F_ext)/m, X += v (Eq. newton, unit time
-//      step); when the node's lower lattice corner changes, the 4x4x4 cells
-//      around the new position are marked active (see lbib_internal.h).
+//   4. after a cluster barrier every block sums, for its share of the
+//      nodes, the C partial force arrays through distributed shared memory in
+//      a fixed order and writes the membrane force of each node.
+// Coupling part, one thread per node: interpolates the fluid velocity
+//   trilinearly from the 8 surrounding lattice nodes (u = 0 on solid rows),
+//   applies the drag F_d = xi (u - v), spreads -F_d with the same weights
+//   (one 16-byte vector atomic per corner) and advances
+//   v += (F + F_d + F_ext)/m, X += v (Eq. newton, unit time step); when the
+//   node's lower lattice corner changes, the 4x4x4 cells around the new
+//   position are marked active (see lbib_internal.h).
 // Node state is kept as hi + lo FP32 pairs (error-free two-sum arithmetic);
 // FP64 is used only for the per-object area and volume totals.
 #pragma once
@@ -266,7 +269,7 @@ __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, 
     const float S = 0.5f * dot(N, N) * inl;
     const f3 G = (1.f / 3.f) * (B + C);  // centroid relative to a
     const float cw = -T.kal * (S - S0) / S - T.kag * dSg;  // local + global area
-    const f3 fv = (T.kv * dV * S * inl / 3.f) * N;          // volume, a third per vertex
+    const f3 fv = (T.kv * dV * S * inl * (1.f / 3.f)) * N;  // volume, a third per vertex
     const f3 wa = -1.f * G, wb = B - G, wc = C - G;
     F.add(tr.x, (cw * rsqrtf(dot(wa, wa))) * wa + fv);
     F.add(tr.y, (cw * rsqrtf(dot(wb, wb))) * wb + fv);
@@ -351,8 +354,9 @@ __device__ __forceinline__ int share_lo32(int n, int r, int C) {
     return r >= C ? n : (int)((((long long)n * r) / C) & ~31LL);
 }
 
-// The whole update of object o by the calling cluster (all C blocks call it).
-__device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int par, float *sh) {
+// The membrane part of object o by the calling cluster (all C blocks call
+// it): writes the membrane force of each of its nodes to s.Fel.
+__device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *sh) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const ObjDev ob = s.obj[o];
@@ -445,16 +449,26 @@ __device__ __forceinline__ void ib_cluster_object(const SimDev &s, int o, int pa
     cl.sync();  // every block's partial forces complete
 
     // 4. this block's share of the nodes: forces summed over the cluster in
-    //    rank order, then coupling and update
+    //    rank order
     for (int p = share_lo(nn, r, C) + threadIdx.x; p < share_lo(nn, r + 1, C); p += blockDim.x) {
         f3 Fp = mk(0.f, 0.f, 0.f);
         for (int j = 0; j < C; ++j) {
             const float *Fj = cl.map_shared_rank(sh, j) + 8 * nn;
             Fp = Fp + mk(Fj[p], Fj[nn + p], Fj[2 * nn + p]);
         }
-        node_update(s, o, f0 + p, Fp, ob.inv_mass, par);
+        s.Fel[f0 + p] = Fp.x;
+        s.Fel[NN + f0 + p] = Fp.y;
+        s.Fel[2 * NN + f0 + p] = Fp.z;
     }
     cl.sync();  // remote reads complete before any block reuses its shared memory
+}
+
+// Coupling part for global node i.
+__device__ __forceinline__ void node_step(const SimDev &s, int i, int par) {
+    const int o = s.node_obj[i];
+    const int NN = s.nn_total;
+    const f3 F = mk(s.Fel[i], s.Fel[NN + i], s.Fel[2 * NN + i]);
+    node_update(s, o, i, F, s.obj[o].inv_mass, par);
 }
 
 }  // namespace lbib

@@ -106,6 +106,8 @@ struct SimDev {
     uint32_t *amask;
     float4 *ufield;
     float *Xh, *Xl, *Vh, *Vl; // [3][nn_total] each
+    float *Fel;               // [3][nn_total] membrane force of the current step
+    const int *node_obj;      // [nn_total] object of each node
     int nn_total, nobj;
     const ObjDev *obj;
     const float *fext;        // [nobj][3] external force per node of each object
@@ -125,8 +127,11 @@ cudaError_t launch_set_pops(const SimDev &s, int pop_par, const double *h_full, 
 cudaError_t launch_mass(const SimDev &s, int pop_par, double *acc, cudaStream_t st);
 
 // ---- launchers (ib.cu) -----------------------------------------------------
-// one cluster of `cluster` blocks per object; max_nodes sizes shared memory
-cudaError_t launch_ib(const SimDev &s, int par, int max_nodes, int cluster, cudaStream_t st);
+// membrane part: clusters of `cluster` blocks, one per object or at most
+// max_clusters (> 0) looping over the objects (max_nodes sizes shared
+// memory); coupling part: one thread per node
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, cudaStream_t st);
+cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st);
 // oid >= 0: one object into out[14]; oid < 0: every object into out[nobj][14]
 cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st);
 cudaError_t launch_analyze(const SimDev &s, int oid, double *out, cudaStream_t st);

@@ -34,7 +34,7 @@ struct lbib_sim {
     bool host_newer = false;     // host mirror changed since the last upload
     bool dev_newer = false;      // device state advanced since the last download
     bool tables_dirty = false;   // object/template tables need an upload
-    float *dnodes = nullptr;     // Xh, Xl, Vh, Vl, each [3][nn_total]
+    float *dnodes = nullptr;     // Xh, Xl, Vh, Vl, Fel, each [3][nn_total], then node_obj [nn_total]
     int dev_nn_cap = 0;
     size_t node_bytes = 0;
     lbib::ObjDev *d_obj = nullptr;
@@ -42,14 +42,24 @@ struct lbib_sim {
     std::vector<float> fext;     // [nobj][3]
     std::vector<double> masses;
     float *d_fext = nullptr;
-    int cluster = 4;             // thread blocks per object in the object kernel
+    int cluster = 1;             // thread blocks per object in the membrane kernel
     bool fext_dirty = false;
     double *d_analyze = nullptr; // [nobj][14] read-out buffer
     int d_obj_cap = 0;
 
+    // The membrane part of step t+1 runs on a second stream while the fluid
+    // part of step t runs on `stream`; events order the two.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_nodes = nullptr;     // node update of the current step done
+    cudaEvent_t ev_membrane = nullptr;  // membrane forces of the next step ready
+    bool fel_valid = false;             // Fel holds the membrane forces of the current node positions
+    bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
+    int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
+
     bool prof_on = false;        // per-phase CUDA-event timing
-    std::vector<cudaEvent_t> prof_ev;
-    size_t prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev;   // 3 per step on `stream`
+    std::vector<cudaEvent_t> prof_aux;  // 2 per membrane launch on `aux`
+    size_t prof_used = 0, prof_aux_used = 0;
 
     bool fluid_ready = false;
     int64_t t = 0;               // steps since lbib_fluid_init (buffer parity)

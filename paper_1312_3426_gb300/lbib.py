@@ -277,6 +277,8 @@ def lbib_objects_analyze(h, n_obj, out=None):
 
 
 LBIB_TUNE_IB_CLUSTER = 0
+LBIB_TUNE_OVERLAP = 1
+LBIB_TUNE_MEMBRANE_CLUSTERS = 2
 
 
 def lbib_set_tuning(h, key, value):
@@ -294,9 +296,10 @@ def lbib_profile_enable(h, on=True):
 
 
 def lbib_profile_read(h):
-    out = np.zeros(4)
+    out = np.zeros(6)
     _check(h, _lib.lbib_profile_read(h, _p(out)))
-    return dict(fluid_ms=out[0], fluid_launches=int(out[1]), ib_ms=out[2], ib_launches=int(out[3]))
+    return dict(fluid_ms=out[0], fluid_launches=int(out[1]), nodes_ms=out[2], nodes_launches=int(out[3]),
+                membrane_ms=out[4], membrane_launches=int(out[5]))
 
 
 def lbib_fluid_mass(h):

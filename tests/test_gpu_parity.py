@@ -177,6 +177,40 @@ def test_objects_crossing_the_periodic_boundary():
     assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
 
 
+@pytest.mark.parametrize("overlap,cluster,mclusters,chunk", [(1, 2, 0, 40), (1, 3, 1, 1), (0, 1, 0, 7), (0, 8, 1, 40)])
+def test_launch_knobs_chunks_and_midrun_node_change(overlap, cluster, mclusters, chunk):
+    """The membrane forces of the next step are computed ahead of time (on a
+    second stream when overlap is on); replacing nodes between calls must
+    discard them.  Knobs and call granularity change no result beyond the
+    order of the FP32 atomics."""
+    sc = _two_object_scene(True)
+    o = oracle.Oracle.from_scene(sc)
+    g = lbib.Sim.from_scene(sc)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_OVERLAP, overlap)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_IB_CLUSTER, cluster)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, mclusters)
+    assert lbib.lbib_get_tuning(g.h, lbib.LBIB_TUNE_OVERLAP) == overlap
+
+    def advance(n):
+        o.step(n)
+        left = n
+        while left:
+            k = min(chunk, left)
+            g.step(k)
+            left -= k
+
+    advance(40)
+    X, _ = o.read_nodes(1)
+    c = X.mean(0)
+    Xd = c + (X - c) * np.array([1.04, 0.97, 1.0])
+    o.object_set_nodes(1, Xd)
+    g.object_set_nodes(1, Xd)
+    advance(40)
+    g.sync()
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+
+
 def test_node_near_wall_drops_force_like_oracle():
     sc = _two_object_scene(True)
     sc.objects[0].origin = (10.3, 3.2, 8.7)   # radius 3: nodes within 0.5 of the wall plane
