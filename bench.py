@@ -1,10 +1,12 @@
 #!/usr/bin/env python3
 """Throughput of the fused LB-IB step on one GB300 (or N replicas).
 
-A step is one pass of the whole hot path over the workload: per-object area
-and volume sums, the five membrane forces, interpolation, drag, spreading and
-node update (one kernel), then the fused D3Q19 pull-stream + BGK/Guo collide
-with bounce-back walls (one kernel).  The default workload is the
+A step is one pass of the whole hot path over the workload: interpolation,
+drag, spreading and node update (one thread per node), then the fused D3Q19
+pull-stream + BGK/Guo collide with bounce-back walls (one kernel); the
+per-object area and volume sums and the five membrane forces of the next
+step (one thread-block cluster per object) run on a second stream beside
+the fluid kernel.  The default workload is the
 256x128x128 channel with 200 Evans-Fung red blood cells (level-3 meshes,
 128,400 nodes), FP32 populations; the populations (628 MB) exceed the L2
 cache, so no flush is needed between steps.
@@ -90,8 +92,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1312_3426_gb300/csrc/fluid_core.cuh", "paper_1312_3426_gb300/csrc/fluid.cu",
-                "paper_1312_3426_gb300/csrc/lbib_internal.h"):
+    for rel in ("paper_1312_3426_gb300/csrc/fluid_core.cuh", "paper_1312_3426_gb300/csrc/fluid.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -99,17 +100,23 @@ def kernel_source_hash():
 
 def profiled_traffic(workload, precision, cells):
     """DRAM bytes per launch of the fluid kernel from the committed ncu
-    summary, when it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fluid_traffic.json")
+    summary (lines ``traffic: workload=.. precision=.. source_hash=..
+    dram_bytes_per_cell=..``), when it was taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_fluid_dram_traffic.md")
     try:
         with open(path) as f:
-            d = json.load(f)
-    except Exception:
+            lines = f.read().splitlines()
+    except OSError:
         return None
-    rec = d.get(f"{workload}/{precision}")
-    if not rec or rec.get("source_hash") != kernel_source_hash():
-        return None
-    return rec["dram_bytes_per_cell"] * cells
+    for ln in lines:
+        if not ln.startswith("traffic:"):
+            continue
+        kv = dict(tok.split("=", 1) for tok in ln.split()[1:] if "=" in tok)
+        if (kv.get("workload") == workload and kv.get("precision") == precision
+                and kv.get("source_hash") == kernel_source_hash()):
+            return round(float(kv["dram_bytes_per_cell"]) * cells)
+    return None
 
 
 class ClockSampler:

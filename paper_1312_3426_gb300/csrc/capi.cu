@@ -35,6 +35,7 @@ bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
     if (nf <= 0 || nf >= (int64_t)1 << 31) return false;
     L.nf = (int)nf;
     L.nfp = (int)align_up((size_t)nf, 64);
+    if ((int64_t)NQ * L.nfp >= ((int64_t)1 << 32)) return false;  // 32-bit population indices
     L.nwords = (L.nf + 31) / 32;
     size_t o = 0;
     const size_t popb = (size_t)NQ * L.nfp * pop_elem_bytes(p.precision);
@@ -303,6 +304,8 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     d.nz = p->nz;
     d.walls = p->walls_y ? 1 : 0;
     d.nyf = L.nyf;
+    d.div_nx.init((uint32_t)p->nx);
+    d.div_nyf.init((uint32_t)L.nyf);
     d.nf = L.nf;
     d.nfp = L.nfp;
     d.nwords = L.nwords;

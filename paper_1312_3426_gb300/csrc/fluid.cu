@@ -24,13 +24,13 @@
 namespace lbib {
 
 template <typename T>
-__global__ void __launch_bounds__(FLUID_THREADS) k_fluid(SimDev s, int par, uint32_t seed) {
+__global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed) {
     fluid_block<T>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st) {
-    const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
     const uint32_t seed = step_seed(t);
+    const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
     switch (s.prec) {
         case LBIB_POP_F32: k_fluid<float><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
         case LBIB_POP_F16S: k_fluid<__half><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;

@@ -17,31 +17,26 @@ namespace lbib {
 // would turn the per-step forcing increment, which is far below one unit in
 // the last place of a 16-bit number once the flow has built up, into a
 // systematic error.  The random bits come from a counter-based hash of
-// (cell, step, direction), so results are reproducible.
+// (cell, step) stepped by a linear congruential generator across the
+// directions, so results are reproducible.
+//
+// PopIO::ld reads a deviation (read-outs and reductions); Raw below is the
+// step kernel's access to the stored numbers themselves.
 template <typename T>
 struct PopIO;
 
 template <>
 struct PopIO<float> {
     static __device__ __forceinline__ float ld(const float *p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float v, float, uint32_t) { __stcs(p, v); }
 };
 template <>
 struct PopIO<__half> {
     static __device__ __forceinline__ float ld(const __half *p, float inv) { return __half2float(__ldg(p)) * inv; }
-    static __device__ __forceinline__ void st(__half *p, float v, float sc, uint32_t rnd) {
-        const uint32_t b = __float_as_uint(v * sc) + (rnd & 0x1fffu);  // 13 bits dropped by FP16
-        *p = __float2half_rz(__uint_as_float(b));
-    }
 };
 template <>
 struct PopIO<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, float inv) {
         return __bfloat162float(__ldg(p)) * inv;
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, float sc, uint32_t rnd) {
-        const uint32_t b = __float_as_uint(v * sc) + (rnd & 0xffffu);  // 16 bits dropped by BF16
-        *p = __float2bfloat16_rz(__uint_as_float(b));
     }
 };
 
@@ -82,55 +77,174 @@ __device__ __forceinline__ Nbr neighbours(const SimDev &s, int x, int y, int z) 
 }
 
 // Pull the population of direction Q arriving at cell f.
+// Raw storage access for the step kernel: the stored number as float (the
+// deviation times 2^s for FP16/BF16), and the store of such a number with
+// the stochastic rounding of PopIO (low bits of rnd).
+template <typename T>
+struct Raw;
+template <>
+struct Raw<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v, uint32_t) { __stcs(p, v); }
+};
+template <>
+struct Raw<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v, uint32_t rnd) {
+        const __half h = __float2half_rz(__uint_as_float(__float_as_uint(v) + (rnd & 0x1fffu)));
+        __stcs((unsigned short *)p, __half_as_ushort(h));
+    }
+};
+template <>
+struct Raw<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
+        return __uint_as_float((uint32_t)__ldg((const unsigned short *)p) << 16);
+    }
+    // round toward zero of the randomised pattern is its upper half
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, uint32_t rnd) {
+        __stcs((unsigned short *)p, (unsigned short)((__float_as_uint(v) + (rnd & 0xffffu)) >> 16));
+    }
+};
+
+// Pull the (raw) population of direction Q arriving at cell f.
 template <typename T, int Q>
-__device__ __forceinline__ float pull(const T *__restrict__ src, int nfp, int f, const Nbr &n, float inv) {
+__device__ __forceinline__ float pull(const T *__restrict__ src, uint32_t nfp, uint32_t f, const Nbr &n) {
     constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
     if ((ey == 1 && n.ylo_solid) || (ey == -1 && n.yhi_solid))
-        return PopIO<T>::ld(src + (size_t)d3q19_opp(Q) * nfp + f, inv);
-    int g = f;
+        return Raw<T>::ld(src + (uint32_t)d3q19_opp(Q) * nfp + f);
+    int g = (int)f;
     if (ex == 1) g += n.dxm;
     if (ex == -1) g += n.dxp;
     if (ey == 1) g += n.dym;
     if (ey == -1) g += n.dyp;
     if (ez == 1) g += n.dzm;
     if (ez == -1) g += n.dzp;
-    return PopIO<T>::ld(src + (size_t)Q * nfp + g, inv);
+    return Raw<T>::ld(src + (uint32_t)Q * nfp + (uint32_t)g);
+}
+
+// Per-cell constants of the collision (see fluid_cell) and the constants
+// of the simulation.
+struct Coll {
+    float K, r45, uG3, om3rho, ux, uy, uz, Gx, Gy, Gz;
+};
+struct CollK {
+    float om, fp, c1, fp3;
+};
+
+// BGK + Guo update of the opposite pair (Q, Q+1) (e_{Q+1} = -e_Q, same
+// weight w), from the split into the parts even and odd in e:
+//   out_{Q/Q+1} = (1 - omega) h + w [A +- B],
+//   A = omega (K + 4.5 rho (e.u)^2) + fpre (9 (e.u)(e.G) - 3 u.G),
+//   B = 3 omega rho (e.u) + 3 fpre (e.G),   K = drho - 1.5 rho u.u,
+// which is h - omega (h - h_eq) + fpre w [3 (e - u) + 9 (e.u) e].G written
+// out for both directions.  wsc = w 2^s (raw storage units).
+// e component E (-1, 0, 1) times v without a multiply; the zero is -0.0f,
+// which the compiler drops from a sum (x + -0 = x for every x), so the
+// dot products and moment sums below carry only their non-zero terms.
+template <int E>
+__device__ __forceinline__ float eterm(float v) {
+    if constexpr (E == 1) return v;
+    else if constexpr (E == -1) return -v;
+    else return -0.0f;
+}
+template <int Q>
+__device__ __forceinline__ float edot(float x, float y, float z) {
+    return eterm<d3q19_ex(Q)>(x) + eterm<d3q19_ey(Q)>(y) + eterm<d3q19_ez(Q)>(z);
+}
+
+// Moments sum h and sum h e from the opposite pairs: h_Q + h_{Q+1} and
+// h_Q - h_{Q+1} for Q = 1, 3, ..., 17.
+struct Moments {
+    float r, x, y, z;
+};
+template <int Q>
+__device__ __forceinline__ void add_pair(Moments &m, float hq, float ho) {
+    const float d = hq - ho;
+    m.r += hq + ho;
+    m.x += eterm<d3q19_ex(Q)>(d);
+    m.y += eterm<d3q19_ey(Q)>(d);
+    m.z += eterm<d3q19_ez(Q)>(d);
+}
+__device__ __forceinline__ Moments moments19(const float (&h)[NQ]) {
+    Moments m{h[0], -0.0f, -0.0f, -0.0f};
+    add_pair<1>(m, h[1], h[2]);
+    add_pair<3>(m, h[3], h[4]);
+    add_pair<5>(m, h[5], h[6]);
+    add_pair<7>(m, h[7], h[8]);
+    add_pair<9>(m, h[9], h[10]);
+    add_pair<11>(m, h[11], h[12]);
+    add_pair<13>(m, h[13], h[14]);
+    add_pair<15>(m, h[15], h[16]);
+    add_pair<17>(m, h[17], h[18]);
+    return m;
+}
+
+// (A + B, A - B) times w 2^s for the opposite pair (Q, Q+1) of one cell.
+template <int Q>
+__device__ __forceinline__ float2 pair_terms(const Coll &c, const CollK &k, float wsc) {
+    const float eu = edot<Q>(c.ux, c.uy, c.uz);
+    const float eG = edot<Q>(c.Gx, c.Gy, c.Gz);
+    const float t = fmaf(c.r45, eu * eu, c.K);
+    const float fs = fmaf(9.0f * eu, eG, -c.uG3);
+    const float A = wsc * fmaf(k.om, t, k.fp * fs);
+    const float B = wsc * fmaf(c.om3rho, eu, k.fp3 * eG);
+    return make_float2(A + B, A - B);
 }
 
 template <typename T, int Q>
-__device__ __forceinline__ void collide_store(T *__restrict__ dst, int nfp, int f, float h, float drho, float rho,
-                                              float ux, float uy, float uz, float usq, float Gx, float Gy,
-                                              float Gz, float omega, float fpre, float sc, uint32_t &rng) {
-    constexpr float ex = (float)d3q19_ex(Q), ey = (float)d3q19_ey(Q), ez = (float)d3q19_ez(Q);
-    constexpr float w = (float)d3q19_w(Q);
-    const float eu = ex * ux + ey * uy + ez * uz;
-    const float heq = w * (drho + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq));
-    const float eG = ex * Gx + ey * Gy + ez * Gz;
-    const float uG = ux * Gx + uy * Gy + uz * Gz;
-    const float Fq = w * (3.0f * (eG - uG) + 9.0f * eu * eG);
-    const float out = h - omega * (h - heq) + fpre * Fq;
-    uint32_t rnd = 0;
-    if (sizeof(T) == 2) {  // one linear-congruential step per population
-        rng = rng * 747796405u + 2891336453u;
-        rnd = rng ^ (rng >> 15);
-    }
-    PopIO<T>::st(dst + (size_t)Q * nfp + f, out, sc, rnd);
+__device__ __forceinline__ void collide_pair(T *__restrict__ dst, uint32_t nfp, uint32_t f, float hq, float ho,
+                                             const Coll &c, const CollK &k, float wsc, uint32_t rnd) {
+    const float2 ab = pair_terms<Q>(c, k, wsc);
+    Raw<T>::st(dst + (uint32_t)Q * nfp + f, fmaf(k.c1, hq, ab.x), rnd);
+    Raw<T>::st(dst + (uint32_t)(Q + 1) * nfp + f, fmaf(k.c1, ho, ab.y), rnd >> 16);
+}
+
+// Collision constants of one cell from the raw moments.
+__device__ __forceinline__ Coll make_coll(const SimDev &s, const CollK &k, float sr, float sx, float sy, float sz,
+                                          float Gx, float Gy, float Gz, float &rho, float &usq) {
+    const float inv = s.inv_scale;
+    const float drho = sr * inv;
+    rho = s.rho0 + drho;
+    const float irho = __fdividef(1.0f, rho);  // rho is near 1: the fast reciprocal is within 2 ulp
+    Coll c;
+    c.ux = fmaf(0.5f, Gx, sx * inv) * irho;
+    c.uy = fmaf(0.5f, Gy, sy * inv) * irho;
+    c.uz = fmaf(0.5f, Gz, sz * inv) * irho;
+    c.Gx = Gx;
+    c.Gy = Gy;
+    c.Gz = Gz;
+    usq = c.ux * c.ux + c.uy * c.uy + c.uz * c.uz;
+    const float uG = c.ux * Gx + c.uy * Gy + c.uz * Gz;
+    c.K = fmaf(-1.5f * rho, usq, drho);
+    c.r45 = 4.5f * rho;
+    c.uG3 = 3.0f * uG;
+    c.om3rho = 3.0f * k.om * rho;
+    return c;
+}
+
+__device__ __forceinline__ CollK make_collk(const SimDev &s) {
+    CollK k;
+    k.om = s.omega;
+    k.fp = s.fpre;
+    k.c1 = 1.0f - s.omega;
+    k.fp3 = 3.0f * s.fpre;
+    return k;
 }
 
 template <typename T>
-__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, bool active, uint32_t step_seed) {
+__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, bool active, uint32_t step_seed) {
+    static_assert(d3q19_opp(1) == 2 && d3q19_opp(17) == 18, "directions 2k-1, 2k must be opposite");
     const T *__restrict__ src = (const T *)s.pop[par];
     T *__restrict__ dst = (T *)s.pop[par ^ 1];
-    const int nfp = s.nfp;
-    const float inv = s.inv_scale;
-    const int x = f % s.nx;
-    const int r = f / s.nx;
-    const int y = r % s.nyf;
-    const int z = r / s.nyf;
-    const Nbr n = neighbours(s, x, y, z);
+    const uint32_t nfp = (uint32_t)s.nfp, f = (uint32_t)fi;
+    const uint32_t r = s.div_nx.div(f);
+    const uint32_t x = f - r * (uint32_t)s.nx;
+    const uint32_t z = s.div_nyf.div(r);
+    const uint32_t y = r - z * (uint32_t)s.nyf;
+    const Nbr n = neighbours(s, (int)x, (int)y, (int)z);
 
     float h[NQ];
-#define LBIB_PULL(q) h[q] = pull<T, q>(src, nfp, f, n, inv);
+#define LBIB_PULL(q) h[q] = pull<T, q>(src, nfp, f, n);
     LBIB_PULL(0) LBIB_PULL(1) LBIB_PULL(2) LBIB_PULL(3) LBIB_PULL(4) LBIB_PULL(5) LBIB_PULL(6)
     LBIB_PULL(7) LBIB_PULL(8) LBIB_PULL(9) LBIB_PULL(10) LBIB_PULL(11) LBIB_PULL(12) LBIB_PULL(13)
     LBIB_PULL(14) LBIB_PULL(15) LBIB_PULL(16) LBIB_PULL(17) LBIB_PULL(18)
@@ -145,29 +259,34 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int f, bool
         s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        drho += h[q];
-        jx += (float)d3q19_ex(q) * h[q];
-        jy += (float)d3q19_ey(q) * h[q];
-        jz += (float)d3q19_ez(q) * h[q];
-    }
-    const float rho = s.rho0 + drho;
-    const float irho = 1.0f / rho;
-    const float ux = (jx + 0.5f * Gx) * irho;
-    const float uy = (jy + 0.5f * Gy) * irho;
-    const float uz = (jz + 0.5f * Gz) * irho;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    const float om = s.omega, fp = s.fpre, sc = s.scale;
-    uint32_t rng = (sizeof(T) == 2) ? mix32((uint32_t)f ^ step_seed) : 0u;
-#define LBIB_COLL(q) collide_store<T, q>(dst, nfp, f, h[q], drho, rho, ux, uy, uz, usq, Gx, Gy, Gz, om, fp, sc, rng);
-    LBIB_COLL(0) LBIB_COLL(1) LBIB_COLL(2) LBIB_COLL(3) LBIB_COLL(4) LBIB_COLL(5) LBIB_COLL(6)
-    LBIB_COLL(7) LBIB_COLL(8) LBIB_COLL(9) LBIB_COLL(10) LBIB_COLL(11) LBIB_COLL(12) LBIB_COLL(13)
-    LBIB_COLL(14) LBIB_COLL(15) LBIB_COLL(16) LBIB_COLL(17) LBIB_COLL(18)
-#undef LBIB_COLL
+    // moments of the raw numbers, then back to deviations (exact: 2^-s)
+    const Moments m = moments19(h);
+    const CollK k = make_collk(s);
+    float rho, usq;
+    const Coll c = make_coll(s, k, m.r, m.x, m.y, m.z, Gx, Gy, Gz, rho, usq);
+    const float sc = s.scale;
+    const float wsc0 = (float)d3q19_w(0) * sc, wsc1 = (float)d3q19_w(1) * sc, wsc2 = (float)d3q19_w(7) * sc;
 
-    if (active) s.ufield[f] = make_float4(ux, uy, uz, rho);
+    // 16 random bits per population for FP16/BF16 (one step of a linear
+    // congruential generator per pair of populations)
+    uint32_t rng = (sizeof(T) == 2) ? mix32(f ^ step_seed) : 0u;
+    auto next = [&]() -> uint32_t {
+        if (sizeof(T) != 2) return 0u;
+        rng = rng * 747796405u + 2891336453u;
+        return rng ^ (rng >> 15);
+    };
+    Raw<T>::st(dst + f, fmaf(k.c1, h[0], wsc0 * fmaf(k.om, c.K, -k.fp * c.uG3)), next());
+    collide_pair<T, 1>(dst, nfp, f, h[1], h[2], c, k, wsc1, next());
+    collide_pair<T, 3>(dst, nfp, f, h[3], h[4], c, k, wsc1, next());
+    collide_pair<T, 5>(dst, nfp, f, h[5], h[6], c, k, wsc1, next());
+    collide_pair<T, 7>(dst, nfp, f, h[7], h[8], c, k, wsc2, next());
+    collide_pair<T, 9>(dst, nfp, f, h[9], h[10], c, k, wsc2, next());
+    collide_pair<T, 11>(dst, nfp, f, h[11], h[12], c, k, wsc2, next());
+    collide_pair<T, 13>(dst, nfp, f, h[13], h[14], c, k, wsc2, next());
+    collide_pair<T, 15>(dst, nfp, f, h[15], h[16], c, k, wsc2, next());
+    collide_pair<T, 17>(dst, nfp, f, h[17], h[18], c, k, wsc2, next());
+
+    if (active) s.ufield[f] = make_float4(c.ux, c.uy, c.uz, rho);
     if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
 }
 

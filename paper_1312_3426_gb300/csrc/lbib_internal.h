@@ -93,8 +93,31 @@ struct ObjDev {
 
 // Everything a kernel needs to know about one simulation (POD, passed by
 // value to single-simulation kernels and stored in an array for batches).
+// Division by a fixed divisor d >= 1 of any 32-bit unsigned n with one
+// multiply-high (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> 1)) >> (l - 1)
+// with t = mulhi(n, m); l = 0 (d = 1) gives q = n.
+struct FastDiv {
+    uint32_t m;
+    int l;
+    void init(uint32_t d) {
+        l = 0;
+        while ((1ull << l) < d) ++l;
+        m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        if (l == 0) return n;
+        const uint32_t t = __umulhi(n, m);
+        return (t + ((n - t) >> 1)) >> (l - 1);
+    }
+#endif
+};
+
 struct SimDev {
     int nx, ny, nz, walls;
+    FastDiv div_nx, div_nyf;  // cell index -> (x, row), row -> (y, z)
     int nyf, nf, nfp, nwords;
     int prec;                 // lbib_precision
     float omega, fpre, rho0;  // 1/tau, 1 - 1/(2 tau), rest density
