@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rbc256", "rbc512", "sphere40"], default="rbc256")
+    ap.add_argument("--workload", choices=["rbc256", "rbc512", "sphere40", "batch64"], default="rbc256")
     ap.add_argument("--precision", choices=["f32", "f16s", "bf16s"], default="f32")
     ap.add_argument("--scale-log2", type=int, default=12, help="storage scale 2^s for f16s/bf16s")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -61,8 +61,12 @@ def parse_args():
                     help="membrane forces overlapped with the fluid step (-1: library default)")
     ap.add_argument("--membrane-clusters", type=int, default=-1,
                     help="clusters of the membrane kernel (0: one per object, -1: library default)")
-    ap.add_argument("--launch", choices=["separate", "persistent"], default="separate",
-                    help="one launch per phase (lbib_step) or one persistent launch per step (lbib_batch_step)")
+    ap.add_argument("--launch", choices=["separate", "batched"], default="separate",
+                    help="lbib_step, or lbib_batch_step (work lists + captured graphs) on the one simulation")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-mlups-estimate", type=float, default=22000.0,
+                    help="batched FP16 throughput used to set the arrival rate (offered load 0.8)")
     return ap.parse_args()
 
 
@@ -204,6 +208,61 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_workload(args, lbib, torch, dev, stream):
+    """64 independent channels (random boxes 32^3..128x64x64, 0-40 cells of
+    level 2/3/4, FP32) advanced together by lbib_batch_step; knobs from the
+    autotuner.  Returns the fields of the JSON line."""
+    from paper_1312_3426_gb300 import tune
+    from workloads import scenes
+    scs = scenes.batch_mix(64)
+    sims = [lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
+                                stream=stream.cuda_stream) for sc in scs]
+    choice, timing = tune.autotune(sims, steps=32, batched=True)
+    h = [s.h for s in sims]
+    lbib.lbib_batch_step(h, max(3, args.warmup))
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbib.lbib_batch_step(h, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    cells = sum(sc.n_fluid_cells for sc in scs)
+    nodes = sum(sc.n_nodes for sc in scs)
+    for s in sims:
+        s.close()
+    return scs, cells, nodes, ms, clocks, {"ib_cluster": choice[0], "overlap": choice[1],
+                                           "candidates_s": {f"{k[0]}/{k[1]}": round(v, 5) for k, v in timing.items()}}
+
+
+def serving_comparison(args, stream):
+    """The request trace served by continuous batching and by the plain
+    one-at-a-time loop (same trace, FP16-shifted storage, 150 GB budget)."""
+    from paper_1312_3426_gb300 import serve
+    from workloads import scenes
+    probe = scenes.serving_trace(n_requests=args.serve_requests, seed=4, rate_per_s=1.0)
+    mean_work = sum(r.scene.n_fluid_cells * r.steps for r in probe) / len(probe)
+    rate = 0.8 * args.serve_mlups_estimate * 1e6 / mean_work
+    reqs = scenes.serving_trace(n_requests=args.serve_requests, seed=4, rate_per_s=rate)
+    kw = dict(precision="f16s", pop_scale_log2=12, budget_bytes=150e9, stream=stream)
+    b = serve.run_trace(reqs, "batched", max_resident=256, chunk_steps=256, **kw)
+    f = serve.run_trace(reqs, "fifo", **kw)
+    return {"trace": f"{len(reqs)} Poisson arrivals at {rate:.2f}/s (offered load 0.8 of "
+                     f"{args.serve_mlups_estimate:.0f} MLUPS), boxes 32^3..192x96x96, 1-100 level-3 RBCs, "
+                     f"1k-20k steps, FP16-shifted, 150 GB budget, seed 4",
+            "batched": b.summary(), "fifo": f.summary(),
+            "p50_speedup": round(f.percentile(50) / max(1e-9, b.percentile(50)), 2),
+            "p99_speedup": round(f.percentile(99) / max(1e-9, b.percentile(99)), 2)}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -233,8 +292,41 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    sc = make_scene(args.workload)
     stream = torch.cuda.current_stream(dev)
+    if args.workload == "batch64":
+        scs, cells, nodes, ms, clocks, tuned = batch_workload(args, lbib, torch, dev, stream)
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        peak, peak_kind = measured_peak()
+        bpc = BYTES_PER_CELL[args.precision]
+        achieved = bpc * cells / (ms / args.steps / 1e3) / 1e9
+        if rank == 0:
+            line = {
+                "metric": METRIC, "value": round(world * cells * args.steps / (ms / 1e3) / 1e6, 2), "unit": "MLUPS",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded batch of channels)",
+                "config": {"workload": f"batch_mix: {len(scs)} channels, boxes 32^3..128x64x64, "
+                                       f"{sum(len(x.objects) for x in scs)} cells (levels 2-4), {nodes} nodes, "
+                                       f"{cells} fluid cells", "tuning": tuned,
+                           "l2": "inputs larger than L2, no flush",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "traffic": None,
+                             "kernel": "whole batched step (all kernels)", "bytes_per_cell": bpc,
+                             "peak_source": peak_kind + " copy bandwidth"},
+                "nodes_per_s": round(world * nodes * args.steps / (ms / 1e3), 1),
+                "gpu_launches": args.steps * 3 + args.steps // 16,
+                "clocks": clocks, "e2e": None, "cpu_baseline": None,
+            }
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    sc = make_scene(args.workload)
     sim = lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
                               stream=stream.cuda_stream)
     nf = sc.n_fluid_cells
@@ -256,7 +348,7 @@ def main():
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
-    persistent = args.launch == "persistent"
+    persistent = args.launch == "batched"
     if not persistent:
         lbib.lbib_profile_enable(sim.h, True)
     e0.record(stream)
@@ -313,6 +405,10 @@ def main():
         e2e = {"value": round(world * nf * k_e2e / float(t.item()) / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": 24 * nobj, "d2h_bytes_per_step": 14 * 8 * nobj}
 
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_comparison(args, stream.cuda_stream)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(sc, args.cpu_seconds)
@@ -329,7 +425,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "k_batch_step" if persistent else f"k_fluid<{args.precision}>",
+                         "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"k_fluid<{args.precision}>",
                          "bytes_per_cell": bpc,
                          "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
             "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "nodes": round(nodes_ms, 5),
@@ -338,11 +434,12 @@ def main():
             "step_hbm_frac": round((bpc * nf + 400 * sc.n_nodes) / (ms / args.steps / 1e3) / 1e9 / peak, 4),
             # per step: fluid, node update and (second stream) membrane
             # kernels; the active-cell mask is rebuilt every 128 steps
-            "gpu_launches": args.steps * (1 if persistent else (3 if sc.objects else 1))
+            "gpu_launches": args.steps * (3 if sc.objects else 1) + (args.steps // 16 if persistent else 0)
             + (args.steps // 128 if sc.objects else 0),
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": base,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     sim.close()

@@ -242,11 +242,43 @@ LBIB_API int lbib_lattice(int32_t *e, double *w);
  * control. */
 LBIB_API int64_t lbib_footprint_bytes(const lbib_fluid_params *params, int64_t n_nodes, int64_t n_tri_total);
 
-/* Advances n simulations (same device) by n_steps each in one persistent
- * launch per phase per step, on the stream of sims[0]; the others' streams
- * are not used.  Each simulation's result equals that of lbib_step on it
- * alone. */
+/* Advances n simulations (same device) by n_steps each (batching; the
+ * paper steps one system at a time).  Each kernel of the step is launched
+ * once for all n simulations over a flat work list, and chunks of steps are
+ * replayed from a captured CUDA graph; the work is ordered on the stream of
+ * sims[0] (the others' pending work is waited for first).  Each
+ * simulation's result equals that of lbib_step on it alone up to the order
+ * of floating-point atomics.  Returns after the steps have completed. */
 LBIB_API lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps);
+
+/* Continuous-batching scheduler for many simulations on one device (no
+ * counterpart in the paper, which runs one system per process: a serving
+ * layer above lbib_batch_step).
+ *   lbib_server_create: budget_bytes caps the device bytes the resident
+ *     simulations hold together (lbib_info out[5]); max_resident caps their
+ *     number; chunk_steps (>= 1) caps the steps of one advance.
+ *   lbib_server_admit: makes sim resident to run n_steps (>= 1) more
+ *     steps; tag is returned when it finishes.  LBIB_ERR_NOMEM when it does
+ *     not fit the budget or no slot is free now (nothing changes; admit it
+ *     after a retirement); LBIB_ERR_ARG for a sim already resident.  The
+ *     caller keeps ownership of sim and must neither step nor destroy it
+ *     while it is resident.
+ *   lbib_server_advance: advances every resident simulation by
+ *     min(chunk_steps, fewest remaining steps) steps in one lbib_batch_step
+ *     and retires those that have no steps left, writing their tags to
+ *     done[0 .. *n_done - 1] (at most cap; the rest retire on the next
+ *     call, which then advances nothing).  *n_done = 0 with nothing resident.
+ *     A simulation whose step fails (its sticky status, see lbib_sync) is
+ *     retired at once with its tag in done; the others are unaffected.
+ *   lbib_server_stats: out[4] = resident simulations, resident bytes,
+ *     advances made, lattice updates done (sum of cells x steps).
+ * The scheduler holds no device memory. */
+typedef struct lbib_server lbib_server;
+LBIB_API lbib_status lbib_server_create(int64_t budget_bytes, int max_resident, int chunk_steps, lbib_server **out);
+LBIB_API void lbib_server_destroy(lbib_server *srv);
+LBIB_API lbib_status lbib_server_admit(lbib_server *srv, lbib_sim *sim, int64_t n_steps, int64_t tag);
+LBIB_API lbib_status lbib_server_advance(lbib_server *srv, int64_t *done, int cap, int *n_done);
+LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
 
 /* Launch-shape knobs, chosen by the autotuner of the Python package or set
  * by hand.  LBIB_TUNE_IB_CLUSTER: thread blocks per object in the

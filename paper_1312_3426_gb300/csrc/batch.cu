@@ -1,26 +1,26 @@
-// Batched step: many independent simulations advanced by one persistent
-// launch per step.
+// Batched step: many independent simulations advanced together.
 //
-// The grid is made of thread-block clusters (as many as fit on the GPU at
-// once).  Phase A: each cluster takes objects, of any simulation, from an
-// atomic ticket (rank 0 draws it and the cluster reads it through
-// distributed shared memory) and updates them as in ib_core.cuh (membrane
-// part, then the coupling part of the object's nodes by the same cluster).  Phase B:
-// once the objects are handed out, every block takes blocks of
-// FLUID_THREADS fluid cells, of any simulation, from a second ticket.  A warp
-// whose 32 cells include active cells (cells near objects, see
-// lbib_internal.h) first waits until all of its simulation's objects are
-// done; the other warps need nothing from this step's object update and run
-// while it is still in progress.
-// Every object was handed out to a running cluster before any block reached
-// phase B, and objects never wait, so every wait ends; it is nevertheless
-// bounded, and on expiry the block flags the simulation (ST_TIMEOUT,
-// surfaced as LBIB_ERR_TIMEOUT) instead of spinning on.
+// A step of the batch is the step of lbib_step (see capi.cu) with every
+// kernel launched once for all simulations over a flat work list:
+//   node kernel      one block per (simulation, run of IB_THREADS nodes)
+//   fluid kernel     one block per (simulation, run of FLUID_THREADS cells),
+//                    one launch per storage type present
+//   membrane kernel  one thread-block cluster per (simulation, object), on a
+//                    second stream while the fluid kernel runs (it prepares
+//                    the next step)
+// so the launch count per step does not grow with the number of
+// simulations, and small simulations fill the GPU together.  Every block
+// reads its simulation's descriptor and step counter from device arrays;
+// the step offset inside a chunk is a kernel argument.  Chunks of
+// LBIB_BATCH_GRAPH_STEPS steps are captured once as a CUDA graph (both
+// streams) and replayed; a small kernel at the end of the graph advances
+// the per-simulation step counters, so one graph serves every chunk of a
+// call and later calls on the same set of simulations.
 //
-// A simulation advanced inside a batch computes what lbib_step computes for
-// it alone: the per-item code is the same device code; only the order of the
-// FP32 vector atomics of the spreading may differ, as between two runs of
-// the single-simulation path.
+// The per-item device code is the code of the single-simulation kernels, so
+// a simulation advanced in a batch computes what lbib_step computes for it
+// alone, up to the order of the FP32 atomics of the spreading and of the
+// membrane-force sums (as between two runs of lbib_step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,185 +33,223 @@
 
 namespace lbib {
 
-constexpr unsigned BATCH_WAIT_SPINS = 1u << 24;  // x ~64 ns: about one second
+constexpr int LBIB_BATCH_GRAPH_STEPS = 16;  // steps per captured graph
 
 extern __shared__ float batch_smem[];
 
-// ib_items: (simulation, object); fl_items: (simulation, block of cells).
-// counters[0]: object ticket; counters[1]: fluid ticket; counters[2 + s]:
-// finished objects of simulation s; need[s]: objects of s.
-__global__ void __launch_bounds__(FLUID_THREADS) k_batch_step(const SimDev *__restrict__ sims,
-                                                              const int *__restrict__ par_base,
-                                                              const long long *__restrict__ t_base, int step_off,
-                                                              const int2 *__restrict__ ib_items, int n_ib,
-                                                              const int2 *__restrict__ fl_items, int n_fl,
-                                                              const int *__restrict__ need, unsigned *counters) {
-    cg::cluster_group cl = cg::this_cluster();
-    __shared__ int s_item;
-    for (;;) {  // phase A: one object per cluster
-        if (cl.block_rank() == 0 && threadIdx.x == 0) s_item = (int)atomicAdd(counters, 1u);
-        cl.sync();
-        const int k = *cl.map_shared_rank(&s_item, 0);
-        cl.sync();  // every block has read the ticket before rank 0 draws again
-        if (k >= n_ib) break;
-        const int2 it = ib_items[k];
-        const SimDev &s = sims[it.x];
-        const int par = (par_base[it.x] + step_off) & 1;
-        membrane_object(s, it.y, batch_smem);
-        // the object's nodes: coupling and update (membrane forces visible
-        // after the cluster barrier that ends membrane_object)
-        {
-            const ObjDev ob = s.obj[it.y];
-            const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
-            for (int p = share_lo(ob.nn, r, C) + threadIdx.x; p < share_lo(ob.nn, r + 1, C); p += blockDim.x)
-                node_step(s, ob.first + p, par);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) __threadfence();  // this block's node updates, device-wide
-        cl.sync();
-        if (cl.block_rank() == 0 && threadIdx.x == 0) atomicAdd(counters + 2 + it.x, 1u);
-    }
-    for (;;) {  // phase B: blocks of fluid cells
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(counters + 1, 1u);
-        __syncthreads();
-        const int k = s_item;
-        __syncthreads();
-        if (k >= n_fl) break;
-        const int2 it = fl_items[k];
-        const SimDev &s = sims[it.x];
-        const int par = (par_base[it.x] + step_off) & 1;
-        const int f = it.y * FLUID_THREADS + (int)threadIdx.x;
-        const uint32_t act = active_word(s, f);  // warp-uniform
-        if (act) {
-            // cells near objects need this step's spread force: wait for the
-            // simulation's objects (warps without such cells go ahead)
-            if ((threadIdx.x & 31) == 0) {
-                const volatile unsigned *done = counters + 2 + it.x;
-                const unsigned want = (unsigned)need[it.x];
-                unsigned spins = 0;
-                while (*done < want) {
-                    __nanosleep(64);
-                    if (++spins > BATCH_WAIT_SPINS) {
-                        atomicOr(s.status, ST_TIMEOUT);
-                        break;
-                    }
-                }
-                __threadfence();
-            }
-            __syncwarp();
-        }
-        if (f < s.nf) {
-            const uint32_t seed = step_seed(t_base[it.x] + step_off);
-            const bool a = (act >> (threadIdx.x & 31)) & 1u;
-            switch (s.prec) {
-                case LBIB_POP_F32: fluid_cell<float>(s, par, f, a, seed); break;
-                case LBIB_POP_F16S: fluid_cell<__half>(s, par, f, a, seed); break;
-                default: fluid_cell<__nv_bfloat16>(s, par, f, a, seed); break;
-            }
-        }
-    }
+// One launch per storage type present in the batch (items grouped by type).
+template <typename T>
+__global__ void __launch_bounds__(FLUID_THREADS, 5)
+    k_batch_fluid(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
+                  const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];  // (simulation, block of cells)
+    const SimDev &s = sims[it.x];
+    const long long t = t_base[it.x] + step_off;
+    fluid_block<T>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
 }
 
-// A batch plan: device copies of the descriptors and the item lists,
-// rebuilt whenever the set of simulations or their objects change.
+__global__ void __launch_bounds__(IB_THREADS, 3)
+    k_batch_nodes(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
+                  const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];  // (simulation, first node)
+    const SimDev &s = sims[it.x];
+    const int i = it.y + (int)threadIdx.x;
+    if (i < s.nn_total) node_step(s, i, (int)((t_base[it.x] + step_off) & 1));
+}
+
+__global__ void __launch_bounds__(IB_THREADS, 4)
+    k_batch_membrane(const SimDev *__restrict__ sims, const int2 *__restrict__ items) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int2 it = items[blockIdx.x / cl.num_blocks()];  // (simulation, object)
+    membrane_object(sims[it.x], it.y, batch_smem);
+}
+
+__global__ void k_batch_advance(long long *t_base, int n, int steps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t_base[i] += steps;
+}
+
+// A batch plan: device copies of the descriptors and the work lists, and
+// the captured graph; rebuilt when the set of simulations, their objects or
+// the cluster size change.
 struct BatchPlan {
     std::vector<lbib_sim *> sims;
-    std::vector<int> nobj;
+    std::vector<uint64_t> serial;  // identity of each simulation (addresses can be reused)
+    std::vector<int> nobj, nn;
+    std::vector<SimDev> dev;  // descriptors the device copy holds
+    int cluster = 0, device = -1;
     SimDev *d_sims = nullptr;
-    int *d_par = nullptr;
     long long *d_t = nullptr;
-    int2 *d_items = nullptr;
-    int *d_need = nullptr;
-    unsigned *d_counters = nullptr;
-    int n_ib = 0, n_fl = 0, cluster = 4, grid = 0;
-    size_t smem = 0;
+    int2 *d_items = nullptr;  // fluid (FP32, FP16S, BF16S), then node, then membrane items
+    int n_flp[3] = {0, 0, 0};  // fluid items per storage type
+    int n_fl = 0, n_nd = 0, n_mb = 0;
+    int max_nodes = 0;
+    cudaStream_t aux = nullptr;   // membrane kernel
+    cudaStream_t gst = nullptr;   // graph launches (the caller's stream may be the legacy one, which cannot be captured)
+    cudaEvent_t ev_nodes = nullptr, ev_membrane = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph = nullptr;
 
+    void release_graph() {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
     void release() {
+        release_graph();
         cudaFree(d_sims);
-        cudaFree(d_par);
         cudaFree(d_t);
         cudaFree(d_items);
-        cudaFree(d_need);
-        cudaFree(d_counters);
         d_sims = nullptr;
-        d_par = nullptr;
         d_t = nullptr;
         d_items = nullptr;
-        d_need = nullptr;
-        d_counters = nullptr;
         sims.clear();
+        serial.clear();
         nobj.clear();
+        nn.clear();
+        dev.clear();
     }
 };
 
 static BatchPlan g_plan;
 
 static bool plan_matches(lbib_sim *const *sims, int n, int cluster) {
-    if ((int)g_plan.sims.size() != n || g_plan.cluster != cluster) return false;
+    if ((int)g_plan.sims.size() != n || g_plan.cluster != cluster || g_plan.device != sims[0]->device) return false;
     for (int i = 0; i < n; ++i)
-        if (g_plan.sims[i] != sims[i] || g_plan.nobj[i] != (int)sims[i]->objs.size()) return false;
+        if (g_plan.sims[i] != sims[i] || g_plan.serial[i] != sims[i]->serial ||
+            g_plan.nobj[i] != (int)sims[i]->objs.size() ||
+            g_plan.nn[i] != sims[i]->nn_total)
+            return false;
     return true;
+}
+
+static cudaError_t set_membrane_attrs(size_t smem) {
+    static size_t configured = 0;
+    if (smem <= configured) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_membrane, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) configured = smem;
+    return e;
 }
 
 static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStream_t st) {
     g_plan.release();
-    std::vector<SimDev> dev(n);
-    std::vector<int2> ib, fl;
-    std::vector<int> need(n);
+    if (!g_plan.aux) {
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g_plan.aux, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g_plan.gst, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_nodes, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_membrane, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    std::vector<int2> flp[3], fl, nd, mb;
     int max_nodes = 0;
     for (int i = 0; i < n; ++i) {
-        dev[i] = sims[i]->d;
-        need[i] = (int)sims[i]->objs.size();
-        max_nodes = std::max(max_nodes, sims[i]->max_nodes);
-        for (int o = 0; o < need[i]; ++o) ib.push_back(make_int2(i, o));
-        const int blocks = (dev[i].nf + FLUID_THREADS - 1) / FLUID_THREADS;
-        for (int b = 0; b < blocks; ++b) fl.push_back(make_int2(i, b));
+        const lbib_sim *s = sims[i];
+        const int blocks = (s->d.nf + FLUID_THREADS - 1) / FLUID_THREADS;
+        for (int b = 0; b < blocks; ++b) flp[s->d.prec].push_back(make_int2(i, b));
+        if (!s->objs.empty()) {
+            for (int f = 0; f < s->nn_total; f += IB_THREADS) nd.push_back(make_int2(i, f));
+            for (int o = 0; o < (int)s->objs.size(); ++o) mb.push_back(make_int2(i, o));
+            max_nodes = std::max(max_nodes, s->max_nodes);
+        }
     }
-    std::vector<int2> items(ib);
-    items.insert(items.end(), fl.begin(), fl.end());
+    for (int k = 0; k < 3; ++k) {
+        g_plan.n_flp[k] = (int)flp[k].size();
+        fl.insert(fl.end(), flp[k].begin(), flp[k].end());
+    }
+    std::vector<int2> items(fl);
+    items.insert(items.end(), nd.begin(), nd.end());
+    items.insert(items.end(), mb.begin(), mb.end());
     cudaError_t e;
     if ((e = cudaMalloc(&g_plan.d_sims, n * sizeof(SimDev))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&g_plan.d_par, n * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&g_plan.d_t, n * sizeof(long long))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&g_plan.d_items, std::max<size_t>(1, items.size()) * sizeof(int2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&g_plan.d_need, n * sizeof(int))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&g_plan.d_counters, (n + 2) * sizeof(unsigned))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(g_plan.d_sims, dev.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return e;
     if (!items.empty() &&
         (e = cudaMemcpyAsync(g_plan.d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
         return e;
-    if ((e = cudaMemcpyAsync(g_plan.d_need, need.data(), n * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     g_plan.sims.assign(sims, sims + n);
-    for (int i = 0; i < n; ++i) g_plan.nobj.push_back((int)sims[i]->objs.size());
-    g_plan.n_ib = (int)ib.size();
+    for (int i = 0; i < n; ++i) {
+        g_plan.serial.push_back(sims[i]->serial);
+        g_plan.nobj.push_back((int)sims[i]->objs.size());
+        g_plan.nn.push_back(sims[i]->nn_total);
+    }
     g_plan.n_fl = (int)fl.size();
+    g_plan.n_nd = (int)nd.size();
+    g_plan.n_mb = (int)mb.size();
     g_plan.cluster = cluster;
-    g_plan.smem = ib_smem_bytes(max_nodes);
-    if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_plan.smem)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
-        return e;
-    // as many clusters as can be resident at once (a persistent grid)
+    g_plan.device = sims[0]->device;
+    g_plan.max_nodes = max_nodes;
+    return g_plan.n_mb ? set_membrane_attrs(ib_smem_bytes(max_nodes)) : cudaSuccess;
+}
+
+static cudaError_t launch_membrane_batch(cudaStream_t st) {
+    if (g_plan.n_mb == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cluster);
-    cfg.blockDim = dim3(FLUID_THREADS);
-    cfg.dynamicSmemBytes = g_plan.smem;
+    cfg.gridDim = dim3((unsigned)(g_plan.n_mb * g_plan.cluster));
+    cfg.blockDim = dim3(IB_THREADS);
+    cfg.dynamicSmemBytes = ib_smem_bytes(g_plan.max_nodes);
+    cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.x = (unsigned)g_plan.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    int clusters = 0;
-    if ((e = cudaOccupancyMaxActiveClusters(&clusters, k_batch_step, &cfg)) != cudaSuccess) return e;
-    g_plan.grid = std::max(1, clusters) * cluster;
-    return cudaSuccess;
+    return cudaLaunchKernelEx(&cfg, k_batch_membrane, (const SimDev *)g_plan.d_sims,
+                              (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd));
+}
+
+// Steps step_off .. step_off + k - 1 relative to the device step counters,
+// on `st` and the plan's second stream; `st` has caught up with the second
+// stream at the end.
+static cudaError_t enqueue_steps(cudaStream_t st, int step_off, int k) {
+    cudaError_t e = cudaSuccess;
+    const int2 *fl = g_plan.d_items, *nd = g_plan.d_items + g_plan.n_fl;
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        const int off = step_off + j;
+        if (g_plan.n_nd) {
+            k_batch_nodes<<<g_plan.n_nd, IB_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if ((e = cudaEventRecord(g_plan.ev_nodes, st)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(g_plan.aux, g_plan.ev_nodes, 0)) != cudaSuccess) break;
+            if ((e = launch_membrane_batch(g_plan.aux)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(g_plan.ev_membrane, g_plan.aux)) != cudaSuccess) break;
+        }
+        const int2 *f16 = fl + g_plan.n_flp[0], *fb16 = f16 + g_plan.n_flp[1];
+        if (g_plan.n_flp[0]) k_batch_fluid<float><<<g_plan.n_flp[0], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, fl);
+        if (g_plan.n_flp[1])
+            k_batch_fluid<__half><<<g_plan.n_flp[1], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, f16);
+        if (g_plan.n_flp[2])
+            k_batch_fluid<__nv_bfloat16>
+                <<<g_plan.n_flp[2], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, fb16);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if (g_plan.n_nd) e = cudaStreamWaitEvent(st, g_plan.ev_membrane, 0);
+    }
+    return e;
+}
+
+// Captures LBIB_BATCH_GRAPH_STEPS steps and the advance of the counters
+// (on the plan's graph stream).
+static cudaError_t capture_graph(cudaStream_t st) {
+    g_plan.release_graph();
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e2 = enqueue_steps(st, 0, LBIB_BATCH_GRAPH_STEPS);
+    if (e2 == cudaSuccess) {
+        const int n = (int)g_plan.sims.size();
+        k_batch_advance<<<(n + 127) / 128, 128, 0, st>>>(g_plan.d_t, n, LBIB_BATCH_GRAPH_STEPS);
+        e2 = cudaGetLastError();
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g_plan.graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
 }
 
 }  // namespace lbib
@@ -233,60 +271,59 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
         if (r != LBIB_OK) return r;
     }
     cudaStream_t st = sims[0]->stream;
-    // other simulations' pending work (uploads, refreshes) must be done
-    for (int i = 1; i < n; ++i)
+    // other simulations' pending work (uploads, refreshes, their own second
+    // streams) must be done
+    for (int i = 0; i < n; ++i) {
         if (sims[i]->stream != st && cudaStreamSynchronize(sims[i]->stream) != cudaSuccess) return LBIB_ERR_CUDA;
+        if (cudaStreamSynchronize(sims[i]->aux) != cudaSuccess) return LBIB_ERR_CUDA;
+    }
     cudaError_t e = cudaSuccess;
     const int cluster = sims[0]->cluster;
-    if (!plan_matches(sims, n, cluster)) {
-        e = build_plan(sims, n, cluster, st);
-        if (e != cudaSuccess) {
-            sims[0]->err = std::string("batch plan: ") + cudaGetErrorString(e);
-            return LBIB_ERR_CUDA;
-        }
-    } else {
-        // descriptors may have changed (node arrays reallocated, tables re-uploaded)
-        std::vector<SimDev> dev(n);
-        for (int i = 0; i < n; ++i) dev[i] = sims[i]->d;
-        e = cudaMemcpyAsync(g_plan.d_sims, dev.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
-    std::vector<int> par(n);
+    if (!plan_matches(sims, n, cluster)) e = build_plan(sims, n, cluster, st);
+    // descriptors (node arrays may have been reallocated, tables uploaded)
+    // and the step counters of this call
     std::vector<long long> tb(n);
-    for (int i = 0; i < n; ++i) {
-        par[i] = (int)(sims[i]->t & 1);
-        tb[i] = (long long)sims[i]->t;
+    for (int i = 0; i < n; ++i) tb[i] = (long long)sims[i]->t;
+    bool same_dev = (int)g_plan.dev.size() == n;
+    for (int i = 0; i < n && same_dev; ++i) same_dev = std::memcmp(&g_plan.dev[i], &sims[i]->d, sizeof(SimDev)) == 0;
+    if (e == cudaSuccess && !same_dev) {
+        g_plan.dev.resize(n);
+        for (int i = 0; i < n; ++i) g_plan.dev[i] = sims[i]->d;
+        e = cudaMemcpyAsync(g_plan.d_sims, g_plan.dev.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g_plan.d_par, par.data(), n * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g_plan.d_t, tb.data(), n * sizeof(long long), cudaMemcpyHostToDevice, st);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)g_plan.grid);
-    cfg.blockDim = dim3(FLUID_THREADS);
-    cfg.dynamicSmemBytes = g_plan.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    const int2 *fl_items = g_plan.d_items + g_plan.n_ib;
-    for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    // membrane forces of the current positions where they are not ready
+    bool need_membrane = false;
+    for (int i = 0; i < n; ++i) need_membrane |= !sims[i]->objs.empty() && !sims[i]->fel_valid;
+    if (e == cudaSuccess && need_membrane && n_steps > 0) e = launch_membrane_batch(st);
+
+    int done = 0;
+    while (e == cudaSuccess && done < n_steps) {
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
             if (sims[i]->since_mark >= ACTIVE_RESET_STEPS) e = sim_remark(sims[i], st);
-            sims[i]->since_mark++;
+        if (e != cudaSuccess) break;
+        const int left = n_steps - done;
+        const int k = left >= LBIB_BATCH_GRAPH_STEPS ? LBIB_BATCH_GRAPH_STEPS : left;
+        if (k == LBIB_BATCH_GRAPH_STEPS) {
+            // the graph advances the device counters by its own step count;
+            // it runs on the graph stream, ordered after and before `st`
+            if (!g_plan.graph) e = capture_graph(g_plan.gst);
+            if (e == cudaSuccess) e = cudaEventRecord(g_plan.ev_join, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(g_plan.gst, g_plan.ev_join, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(g_plan.graph, g_plan.gst);
+            if (e == cudaSuccess) e = cudaEventRecord(g_plan.ev_join, g_plan.gst);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g_plan.ev_join, 0);
+        } else {
+            e = enqueue_steps(st, 0, k);
         }
-        if (e != cudaSuccess) break;
-        e = cudaMemsetAsync(g_plan.d_counters, 0, (n + 2) * sizeof(unsigned), st);
-        if (e != cudaSuccess) break;
-        e = cudaLaunchKernelEx(&cfg, k_batch_step, (const SimDev *)g_plan.d_sims, (const int *)g_plan.d_par,
-                               (const long long *)g_plan.d_t, k, (const int2 *)g_plan.d_items, g_plan.n_ib, fl_items,
-                               g_plan.n_fl, (const int *)g_plan.d_need, g_plan.d_counters);
+        for (int i = 0; i < n; ++i) sims[i]->since_mark += k;
+        done += k;
     }
-    // host copies of par/dev must outlive the async copies
+    // host copies of the descriptors and counters must outlive the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_plan.release();
         for (int i = 0; i < n; ++i) {
             sims[i]->sticky = LBIB_ERR_CUDA;
             sims[i]->err = std::string("batch step: ") + cudaGetErrorString(e);
@@ -295,13 +332,13 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     }
     for (int i = 0; i < n; ++i) {
         lbib_sim *s = sims[i];
-        for (int k = 0; k < n_steps; ++k) {
-            s->gmode = (int)(s->t & 1);
-            s->t++;
-        }
-        if (n_steps > 0 && s->nn_total > 0) {
-            s->dev_newer = true;
-            s->fel_valid = false;  // membrane forces are those of the last step, not the next
+        if (n_steps > 0) {
+            s->gmode = (int)((s->t + n_steps - 1) & 1);
+            s->t += n_steps;
+            if (s->nn_total > 0) {
+                s->dev_newer = true;
+                s->fel_valid = true;  // the last membrane pass used the final positions
+            }
         }
     }
     return LBIB_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -283,7 +284,9 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     if (p->precision < 0 || p->precision > 2 || p->pop_scale_log2 < 0 || p->pop_scale_log2 > 30) return LBIB_ERR_ARG;
     FluidLayout L;
     if (!fluid_layout(*p, L)) return LBIB_ERR_ARG;
+    static std::atomic<uint64_t> next_serial{1};
     lbib_sim *s = new lbib_sim();
+    s->serial = next_serial++;
     s->p = *p;
     s->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&s->device) != cudaSuccess) {

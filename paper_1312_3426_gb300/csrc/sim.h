@@ -13,6 +13,7 @@
 
 struct lbib_sim {
     lbib_fluid_params p{};
+    uint64_t serial = 0;         // unique per simulation of the process (an address may be reused)
     cudaStream_t stream = nullptr;
     int device = 0;
     std::string err;

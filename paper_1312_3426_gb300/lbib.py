@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_lbib.so")
 _lib = None
 
 LBIB_OK = 0
+LBIB_ERR_ARG = -1
+LBIB_ERR_NOMEM = -4
 STATUS_NAMES = {
     0: "LBIB_OK", -1: "LBIB_ERR_ARG", -2: "LBIB_ERR_ID", -3: "LBIB_ERR_MESH", -4: "LBIB_ERR_NOMEM",
     -5: "LBIB_ERR_UNSTABLE", -6: "LBIB_ERR_TIMEOUT", -7: "LBIB_ERR_CUDA", -8: "LBIB_ERR_STATE",
@@ -89,6 +91,11 @@ def load(path: str = LIB_PATH):
         "lbib_get_tuning": (st, [P, C.c_int, C.POINTER(C.c_int)]),
         "lbib_profile_read": (st, [P, P]),
         "lbib_abi_version": (C.c_int, []),
+        "lbib_server_create": (st, [C.c_int64, C.c_int, C.c_int, C.POINTER(P)]),
+        "lbib_server_destroy": (None, [P]),
+        "lbib_server_admit": (st, [P, P, C.c_int64, C.c_int64]),
+        "lbib_server_advance": (st, [P, P, C.c_int, C.POINTER(C.c_int)]),
+        "lbib_server_stats": (st, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -342,6 +349,46 @@ def lbib_batch_step(handles, n_steps=1):
 
 def lbib_abi_version():
     return int(load().lbib_abi_version())
+
+
+def lbib_server_create(budget_bytes, max_resident, chunk_steps):
+    load()
+    out = C.c_void_p()
+    st = _lib.lbib_server_create(int(budget_bytes), int(max_resident), int(chunk_steps), C.byref(out))
+    if st != LBIB_OK:
+        raise LbibError(st, "lbib_server_create")
+    return out
+
+
+def lbib_server_destroy(srv):
+    _lib.lbib_server_destroy(srv)
+
+
+def lbib_server_admit(srv, h, n_steps, tag):
+    """True when admitted, False when the budget or the slots are full."""
+    st = _lib.lbib_server_admit(srv, h, int(n_steps), int(tag))
+    if st == LBIB_ERR_NOMEM:
+        return False
+    if st != LBIB_OK:
+        raise LbibError(st, _lib.lbib_last_error(h).decode() if st != LBIB_ERR_ARG else "lbib_server_admit")
+    return True
+
+
+def lbib_server_advance(srv, cap=1024):
+    done = np.zeros(max(1, cap), np.int64)
+    n = C.c_int(0)
+    st = _lib.lbib_server_advance(srv, _p(done), int(cap), C.byref(n))
+    if st != LBIB_OK:
+        raise LbibError(st, "lbib_server_advance")
+    return [int(t) for t in done[:n.value]]
+
+
+def lbib_server_stats(srv):
+    out = np.zeros(4, np.int64)
+    st = _lib.lbib_server_stats(srv, _p(out))
+    if st != LBIB_OK:
+        raise LbibError(st, "lbib_server_stats")
+    return dict(resident=int(out[0]), resident_bytes=int(out[1]), advances=int(out[2]), updates=int(out[3]))
 
 
 # ----------------------------------------------------------------- convenience

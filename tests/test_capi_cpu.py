@@ -92,3 +92,21 @@ def test_footprint_accounts_for_storage_precision():
     assert b32 >= 2 * 19 * 4 * nf and b16 >= 2 * 19 * 2 * nf
     assert b32 - b16 >= 2 * 19 * 2 * nf
     assert lbib.lbib_footprint_bytes(p32, 1000, 2000) > b32
+
+
+def test_server_host_logic_without_gpu():
+    """The scheduler's argument checks and empty-state behaviour are host
+    code: no device call happens before a simulation is admitted."""
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_server_create(0, 4, 16)
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_server_create(1 << 30, 0, 16)
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_server_create(1 << 30, 4, 0)
+    srv = lbib.lbib_server_create(1 << 30, 4, 16)
+    try:
+        assert lbib.lbib_server_stats(srv) == dict(resident=0, resident_bytes=0, advances=0, updates=0)
+        assert lbib.lbib_server_advance(srv) == []
+        assert lbib.lbib_server_stats(srv)["advances"] == 0
+    finally:
+        lbib.lbib_server_destroy(srv)
