@@ -21,7 +21,12 @@ Printed JSON line (rank 0):
                host memory, steps, and reads every object's analysis back
   cpu_baseline the FP64 oracle on the host cores, a bounded number of full
                steps of the same workload
-``--impl reference`` times that oracle alone on the same workload.
+  serving      a seeded Poisson trace of 256 channel requests (FP16-shifted
+               storage, 150 GB budget) served by continuous batching
+               (lbib_server_*) and by the plain one-at-a-time loop: p50/p99
+               completion latency and aggregate MLUPS of both
+``--impl reference`` times that oracle alone on the same workload;
+``--workload batch64`` measures 64 independent channels advanced together.
 """
 from __future__ import annotations
 
@@ -82,6 +87,25 @@ def make_scene(name):
 def workload_desc(sc):
     return (f"{sc.name}: {len(sc.objects)} objects, {sc.n_nodes} nodes, "
             f"{sc.n_fluid_cells} fluid cells, tau={sc.tau}, body force {sc.body_force[0]:g}")
+
+
+def max_over_ranks(x, device=None):
+    """The largest of x over all ranks of the default process group (x
+    itself without one); device: where the reduction tensor lives (the
+    rank's GPU for NCCL, None for CPU / gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(units_per_rank, steps, ms_max, world):
+    """Replicas: every rank advances its own copy of the workload, so the job
+    processes world x units per step in the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3) / 1e6
 
 
 def measured_peak():
@@ -295,16 +319,13 @@ def main():
     stream = torch.cuda.current_stream(dev)
     if args.workload == "batch64":
         scs, cells, nodes, ms, clocks, tuned = batch_workload(args, lbib, torch, dev, stream)
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         peak, peak_kind = measured_peak()
         bpc = BYTES_PER_CELL[args.precision]
         achieved = bpc * cells / (ms / args.steps / 1e3) / 1e9
         if rank == 0:
             line = {
-                "metric": METRIC, "value": round(world * cells * args.steps / (ms / 1e3) / 1e6, 2), "unit": "MLUPS",
+                "metric": METRIC, "value": round(whole_job_mlups(cells, args.steps, ms, world), 2), "unit": "MLUPS",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded batch of channels)",
@@ -362,12 +383,8 @@ def main():
     prof = lbib.lbib_profile_read(sim.h) if not persistent else None
     lbib.lbib_profile_enable(sim.h, False)
     sim.sync()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * nf * args.steps / (ms / 1e3) / 1e6
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    value = whole_job_mlups(nf, args.steps, ms, world)
 
     if prof is not None:
         fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
@@ -398,11 +415,8 @@ def main():
             else:
                 sim.sync()
         barrier()
-        dt = time.perf_counter() - t0
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": round(world * nf * k_e2e / float(t.item()) / 1e6, 2), "unit": "MLUPS",
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": round(whole_job_mlups(nf, k_e2e, dt * 1e3, world), 2), "unit": "MLUPS",
                "h2d_bytes_per_step": 24 * nobj, "d2h_bytes_per_step": 14 * 8 * nobj}
 
     serving = None
