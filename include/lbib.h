@@ -226,6 +226,22 @@ LBIB_API lbib_status lbib_profile_read(lbib_sim *sim, double out[6]);
 /* Total fluid mass sum_cells sum_i f_i, an FP64 reduction on the GPU. */
 LBIB_API lbib_status lbib_fluid_mass(lbib_sim *sim, double *mass);
 
+/* The same total as lbib_fluid_mass without allocating anything (the paper
+ * has no counterpart: its mass check is not part of the method).  For
+ * callers that cannot allocate device memory: a serving process that has
+ * admitted simulations up to its device-memory budget (an allocation there
+ * can fail or evict), and host loops that must not call into the allocator
+ * between steps.  Each thread block writes its FP64 partial to its own slot
+ * of a static 1024-double scratch array of the library (one per device per
+ * process); the host adds the slots in block order, so the result is
+ * deterministic.  Limit: the reduction grid (4 blocks per SM) must fit the
+ * 1024 slots, i.e. devices with up to 256 SMs; otherwise LBIB_ERR_ARG.
+ * Calls that overlap in time on the same device (other threads, other
+ * streams) race on the one scratch array and must be serialised by the
+ * caller; the call waits for the simulation's stream before returning, so
+ * calls made one after another are safe. */
+LBIB_API lbib_status lbib_fluid_mass_noalloc(lbib_sim *sim, double *mass);
+
 /* Counts (oif_info, Sec. 5).  out[8] = n_templates, n_objects, n_nodes,
  * fluid cells, steps taken, device bytes held, precision, reserved. */
 LBIB_API lbib_status lbib_info(const lbib_sim *sim, int64_t out[8]);

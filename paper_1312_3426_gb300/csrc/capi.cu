@@ -835,6 +835,35 @@ lbib_status lbib_fluid_mass(lbib_sim *s, double *mass) {
     return LBIB_OK;
 }
 
+// Allocation-free form of lbib_fluid_mass (see include/lbib.h): no
+// cudaMalloc / cudaMallocAsync / cudaFree and no pinned host buffer; the
+// partials live in the library's static device scratch and come back into
+// a stack array.
+lbib_status lbib_fluid_mass_noalloc(lbib_sim *s, double *mass) {
+    LBIB_GUARD(s);  // makes the simulation's device current
+    if (!mass) return fail(s, LBIB_ERR_ARG, "null output");
+    if (!s->fluid_ready) return fail(s, LBIB_ERR_STATE, "fluid not initialised");
+    int sms = 0;
+    LBIB_CUDA(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device), "device attribute");
+    int blocks = 4 * sms;
+    const int need = (s->d.nf + 255) / 256;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    if (blocks > MASS_SCRATCH_SLOTS)
+        return fail(s, LBIB_ERR_ARG, "the reduction grid would need more partial slots than the static scratch holds");
+    double *part = nullptr;
+    LBIB_CUDA(s, mass_scratch(&part), "static scratch address");
+    double host[MASS_SCRATCH_SLOTS];
+    cudaError_t e = launch_mass_partials(s->d, (int)(s->t & 1), part, blocks, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, part, (size_t)blocks * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "mass");
+    double dev = 0.0;
+    for (int b = 0; b < blocks; ++b) dev += host[b];
+    *mass = (double)s->d.nf * s->p.rho0 + dev;
+    return LBIB_OK;
+}
+
 lbib_status lbib_info(const lbib_sim *s, int64_t out[8]) {
     if (!s || !out) return LBIB_ERR_ARG;
     out[0] = (int64_t)s->topo.size();

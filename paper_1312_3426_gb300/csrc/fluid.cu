@@ -17,6 +17,7 @@
 // (152 B in FP32, 76 B in FP16/BF16), plus one 4-byte mask word per 32
 // cells for each of the three masks, plus 16 B reads/writes only at cells
 // touched by the immersed objects.
+#include <mutex>
 #include <type_traits>
 
 #include "fluid_core.cuh"
@@ -236,6 +237,59 @@ __global__ void __launch_bounds__(256) k_mass(SimDev s, int par, double *acc) {
         v = warp_sum(v);
         if (threadIdx.x == 0) atomicAdd(acc, v);
     }
+}
+
+// Allocation-free variant: each block writes its FP64 partial sum to its own
+// slot of a fixed scratch array in the library's static device memory, and
+// the host adds the slots in block order (so the result is also
+// independent of scheduling).  One scratch array per device per process.
+static __device__ __align__(256) double g_mass_scratch[MASS_SCRATCH_SLOTS];
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass_partials(SimDev s, int par, double *part) {
+    double local = 0.0;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < s.nf; f += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) local += (double)ld_pop<T>(s, par, q, f);
+    }
+    local = warp_sum(local);
+    __shared__ double wpart[8];
+    if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wpart[w];
+        part[blockIdx.x] = v;  // every slot below gridDim.x is written: nothing to clear
+    }
+}
+
+cudaError_t mass_scratch(double **ptr) {
+    // resolved once per device, with that device current (the caller's)
+    static std::mutex mu;
+    static double *addr[MASS_SCRATCH_DEVICES] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MASS_SCRATCH_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_mass_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = (double *)p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_mass_partials(const SimDev &s, int par, double *part, int blocks, cudaStream_t st) {
+    switch (s.prec) {
+        case LBIB_POP_F32: k_mass_partials<float><<<blocks, 256, 0, st>>>(s, par, part); break;
+        case LBIB_POP_F16S: k_mass_partials<__half><<<blocks, 256, 0, st>>>(s, par, part); break;
+        case LBIB_POP_BF16S: k_mass_partials<__nv_bfloat16><<<blocks, 256, 0, st>>>(s, par, part); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mass(const SimDev &s, int par, double *acc, cudaStream_t st) {

@@ -148,6 +148,12 @@ cudaError_t launch_set_coupling(const SimDev &s, int gpar, const float *g_full, 
 cudaError_t launch_read_pops(const SimDev &s, int pop_par, double *h_full, cudaStream_t st);
 cudaError_t launch_set_pops(const SimDev &s, int pop_par, const double *h_full, cudaStream_t st);
 cudaError_t launch_mass(const SimDev &s, int pop_par, double *acc, cudaStream_t st);
+// allocation-free mass reduction: per-block partials into a static scratch
+// array of MASS_SCRATCH_SLOTS doubles (8 KB) per device
+constexpr int MASS_SCRATCH_SLOTS = 1024;
+constexpr int MASS_SCRATCH_DEVICES = 64;
+cudaError_t mass_scratch(double **ptr);
+cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int blocks, cudaStream_t st);
 
 // ---- launchers (ib.cu) -----------------------------------------------------
 // membrane part: clusters of `cluster` blocks, one per object or at most

@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         "lbib_set_populations": (st, [P, P, C.c_int64]),
         "lbib_object_analyze": (st, [P, C.c_int, P]),
         "lbib_fluid_mass": (st, [P, P]),
+        "lbib_fluid_mass_noalloc": (st, [P, P]),
         "lbib_info": (st, [P, P]),
         "lbib_dropped_momentum": (st, [P, P]),
         "lbib_lattice": (C.c_int, [P, P]),
@@ -307,6 +308,12 @@ def lbib_profile_read(h):
     _check(h, _lib.lbib_profile_read(h, _p(out)))
     return dict(fluid_ms=out[0], fluid_launches=int(out[1]), nodes_ms=out[2], nodes_launches=int(out[3]),
                 membrane_ms=out[4], membrane_launches=int(out[5]))
+
+
+def lbib_fluid_mass_noalloc(h):
+    out = np.zeros(1)
+    _check(h, _lib.lbib_fluid_mass_noalloc(h, _p(out)))
+    return float(out[0])
 
 
 def lbib_fluid_mass(h):
