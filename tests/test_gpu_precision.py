@@ -46,7 +46,7 @@ def profile():
 
 
 @pytest.mark.parametrize("prec,scale,bound,drift_bound",
-                         [("f32", 0, 1e-3, 1e-7), ("f16s", 12, 1e-3, 2e-6), ("bf16s", 12, 2e-2, 2e-5)])
+                         [("f32", 0, 1e-3, 1e-6), ("f16s", 12, 1e-3, 5e-6), ("bf16s", 12, 2e-2, 5e-5)])
 def test_channel_profile_and_mass_drift_512x256x256(profile, prec, scale, bound, drift_bound):
     g = lbib.Sim(NX, NY, NZ, walls=True, tau=1.0, rho0=1.0, body_force=(1e-5, 0.0, 0.0), friction=0.05,
                  precision=prec, pop_scale_log2=scale)
