@@ -67,6 +67,8 @@ def _load():
         "oracle_fluid_init": (None, [P]),
         "oracle_step": (None, [P, C.c_int]),
         "oracle_step_nodes_only": (None, [P, C.c_int]),
+        "oracle_set_repulsion": (C.c_int, [P, dp, dp]),
+        "oracle_repulsion_forces": (None, [P, dp]),
         "oracle_read_velocity": (None, [P, dp]),
         "oracle_set_velocity": (None, [P, dp]),
         "oracle_read_density": (None, [P, dp]),
@@ -124,6 +126,9 @@ class Oracle:
                 oid = o.object_add(ob.tid, ob.origin, ob.rotate, ob.mass)
                 if any(ob.force):
                     o.object_set_force(oid, ob.force)
+        rep = getattr(scene, "repulsion", None)
+        if rep is not None:
+            o.set_repulsion(*rep)
         o.fluid_init()
         return o
 
@@ -195,6 +200,21 @@ class Oracle:
         return F
 
     # fluid --------------------------------------------------------------
+    def set_repulsion(self, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
+        """Soft-sphere repulsion (a, n, cutoff) between objects and against the walls."""
+        rc = self._lib.oracle_set_repulsion(self._h, np.ascontiguousarray(obj, dtype=np.float64),
+                                            np.ascontiguousarray(wall, dtype=np.float64))
+        if rc != 0:
+            raise ValueError("invalid repulsion parameters")
+
+    def n_nodes(self):
+        return sum(self._lib.oracle_object_nodes(self._h, o) for o in range(self.n_objects))
+
+    def repulsion_forces(self):
+        F = np.zeros(3 * self.n_nodes())
+        self._lib.oracle_repulsion_forces(self._h, F)
+        return F.reshape(-1, 3)
+
     def fluid_init(self):
         self._lib.oracle_fluid_init(self._h)
 

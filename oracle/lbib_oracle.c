@@ -67,8 +67,14 @@ typedef struct {
     double mass, fext[3];
 } oobj;
 
+/* Soft-sphere repulsion parameters: amplitude a, exponent n, cutoff rc. */
+typedef struct {
+    double a, n, rc;
+} osoft;
+
 typedef struct osim {
     int nx, ny, nz, walls;
+    osoft rep_obj, rep_wall;  /* object-object and object-wall repulsion (a = 0: off) */
     double tau, rho0, g[3], xi;
     long ncell;
     double *f, *fpost;        /* [ncell][NQ] */
@@ -662,8 +668,75 @@ void oracle_fluid_init(osim *s)
     }
 }
 
-/* One full step, in the order: object measures and elastic forces (Sec. 4),
- * interpolation, drag, spreading and Newton update of the nodes (Sec. 2),
+/* ------------------------------------------------------- repulsion */
+
+/* Object-object and object-wall repulsion.  The example of Sec. 6 sets
+ * "soft-sphere" interactions between the two objects and between each
+ * object and the channel boundaries, with an amplitude a, an exponent n, a
+ * cutoff and an offset; the paper does not print the potential.  Reading:
+ * the usual soft-sphere pair potential V(r) = a r^-n for r < cutoff (offset
+ * 0), so two nodes of different objects at distance r < cutoff push each
+ * other apart along their separation with a force of magnitude a n
+ * r^-(n+1); a node at distance d < cutoff from a wall plane (y = 1 or
+ * y = ny-1) is pushed away from it with a n max(d, 1e-3)^-(n+1) (the floor
+ * keeps a node that reached the plane finite).  Separations use the
+ * minimum image in the periodic directions. */
+static double soft_force(const osoft *p, double r) { return p->a * p->n * pow(r, -(p->n + 1.0)); }
+
+static void repulsion(const osim *s, double *F)
+{
+    if (s->rep_obj.a != 0.0 && s->rep_obj.rc > 0.0) {
+        const double L[3] = {s->nx, s->ny, s->nz};
+        for (int oa = 0; oa < s->nobj; ++oa)
+            for (int ob = oa + 1; ob < s->nobj; ++ob) {
+                const oobj *A = &s->obj[oa], *B = &s->obj[ob];
+                const int na = s->tpl[A->tid].nn, nb = s->tpl[B->tid].nn;
+                for (int i = A->first; i < A->first + na; ++i)
+                    for (int j = B->first; j < B->first + nb; ++j) {
+                        double d[3];
+                        sub3(s->X + 3 * i, s->X + 3 * j, d);
+                        for (int k = 0; k < 3; ++k)
+                            if (k != 1 || !s->walls) d[k] -= L[k] * round(d[k] / L[k]);
+                        const double r = norm3(d);
+                        if (!(r < s->rep_obj.rc) || r <= 0.0) continue;
+                        const double f = soft_force(&s->rep_obj, r) / r;
+                        for (int k = 0; k < 3; ++k) {
+                            F[3 * i + k] += f * d[k];
+                            F[3 * j + k] -= f * d[k];
+                        }
+                    }
+            }
+    }
+    if (s->walls && s->rep_wall.a != 0.0 && s->rep_wall.rc > 0.0) {
+        for (int i = 0; i < s->nnode; ++i) {
+            const double y = s->X[3 * i + 1];
+            const double dlo = y - 1.0, dhi = (s->ny - 1.0) - y;
+            if (dlo < s->rep_wall.rc) F[3 * i + 1] += soft_force(&s->rep_wall, dlo > 1e-3 ? dlo : 1e-3);
+            if (dhi < s->rep_wall.rc) F[3 * i + 1] -= soft_force(&s->rep_wall, dhi > 1e-3 ? dhi : 1e-3);
+        }
+    }
+}
+
+int oracle_set_repulsion(osim *s, const double *obj3, const double *wall3)
+{
+    if (!obj3 || !wall3) return -1;
+    for (int k = 0; k < 3; ++k)
+        if (!(obj3[k] >= 0.0) || !(wall3[k] >= 0.0)) return -1;
+    s->rep_obj.a = obj3[0]; s->rep_obj.n = obj3[1]; s->rep_obj.rc = obj3[2];
+    s->rep_wall.a = wall3[0]; s->rep_wall.n = wall3[1]; s->rep_wall.rc = wall3[2];
+    return 0;
+}
+
+/* Repulsion forces of every node at the current positions (cleared first). */
+void oracle_repulsion_forces(const osim *s, double *F)
+{
+    memset(F, 0, sizeof(double) * 3 * (size_t)s->nnode);
+    repulsion(s, F);
+}
+
+/* One full step, in the order: object measures and elastic forces (Sec. 4)
+ * plus the repulsion (Sec. 6 interactions, when set), interpolation, drag,
+ * spreading and Newton update of the nodes (Sec. 2),
  * then collision and propagation of the fluid (Eq. lbequation) under the
  * body force plus the spread force. */
 void oracle_step(osim *s, int nsteps)
@@ -675,6 +748,7 @@ void oracle_step(osim *s, int nsteps)
             const oobj *ob = &s->obj[o];
             membrane_forces(&s->tpl[ob->tid], s->X + 3 * ob->first, s->Fel + 3 * ob->first, 31);
         }
+        repulsion(s, s->Fel);
         couple_and_move(s);
         collide(s);
         stream(s);
@@ -692,6 +766,7 @@ void oracle_step_nodes_only(osim *s, int nsteps)
             const oobj *ob = &s->obj[o];
             membrane_forces(&s->tpl[ob->tid], s->X + 3 * ob->first, s->Fel + 3 * ob->first, 31);
         }
+        repulsion(s, s->Fel);
         couple_and_move(s);
     }
 }

@@ -74,6 +74,9 @@ class Scene:
     # exchange of 0.05 of the relative velocity per step for unit node mass
     friction: float = 0.05
     steps: int = 1000
+    # soft-sphere repulsion ((a, n, cutoff) object-object, (a, n, cutoff)
+    # object-wall), or None for none
+    repulsion: tuple = None
     templates: list = field(default_factory=list)
     objects: list = field(default_factory=list)
 
