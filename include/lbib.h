@@ -145,6 +145,21 @@ LBIB_API lbib_status lbib_mesh_check(const double *nodes_xyz, int n_nodes, const
 LBIB_API lbib_status lbib_object_add(lbib_sim *sim, int oid, int tid, const double origin[3],
                             const double rotate[3], double mass);
 
+/* Soft-sphere repulsion between objects and against the walls (the
+ * object-object and object-wall "soft-sphere" interactions of the example
+ * in Sec. 6; the paper names the potential and its parameters only).
+ * object[3] = (a, n, cutoff) for pairs of nodes of different objects:
+ * nodes at distance r < cutoff push each other apart with a force of
+ * magnitude a n r^-(n+1) (the potential a r^-n, offset 0).  wall[3] =
+ * (a, n, cutoff) for a node at distance d < cutoff from a wall plane
+ * (y = 1 or y = ny-1): pushed away with a n max(d, 1e-3)^-(n+1).  a = 0
+ * switches a term off (the default).  Separations use the nearest periodic
+ * image; the object cutoff must be below half of every periodic box length
+ * (LBIB_ERR_ARG otherwise, and for a < 0, n <= 0 with a > 0, cutoff < 0).
+ * Evaluated with the membrane forces, on the node positions of the step.
+ * At most 32 close object pairs per object (sticky LBIB_ERR_NOMEM beyond). */
+LBIB_API lbib_status lbib_set_repulsion(lbib_sim *sim, const double object[3], const double wall[3]);
+
 /* External force on every node of an object (Sec. 5, object customization). */
 LBIB_API lbib_status lbib_object_set_force(lbib_sim *sim, int oid, const double f[3]);
 

@@ -185,6 +185,15 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
     return g_plan.n_mb ? set_membrane_attrs(ib_smem_bytes(max_nodes)) : cudaSuccess;
 }
 
+static cudaError_t launch_repulsion_batch(cudaStream_t st) {
+    for (lbib_sim *s : g_plan.sims) {
+        if (!s->d.rep_on) continue;
+        cudaError_t e = launch_repulsion(s->d, s->max_nodes, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t launch_membrane_batch(cudaStream_t st) {
     if (g_plan.n_mb == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
@@ -199,8 +208,10 @@ static cudaError_t launch_membrane_batch(cudaStream_t st) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_membrane, (const SimDev *)g_plan.d_sims,
-                              (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_membrane, (const SimDev *)g_plan.d_sims,
+                                       (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd));
+    // object-object repulsion of the simulations that set it (per simulation)
+    return e == cudaSuccess ? launch_repulsion_batch(st) : e;
 }
 
 // Steps step_off .. step_off + k - 1 relative to the device step counters,

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -109,6 +110,9 @@ lbib_status sim_check_status(lbib_sim *s) {
     if (st & ST_TIMEOUT) {
         s->sticky = LBIB_ERR_TIMEOUT;
         s->err = "a bounded device-side wait gave up";
+    } else if (st & ST_PAIRS) {
+        s->sticky = LBIB_ERR_NOMEM;
+        s->err = "more close object pairs than the repulsion pair list holds";
     } else if (st & (ST_UNSTABLE | ST_NODE_NAN)) {
         s->sticky = LBIB_ERR_UNSTABLE;
         s->err = (st & ST_UNSTABLE) ? "fluid became unstable (NaN or |u| > 0.3)" : "a node position became non-finite";
@@ -166,6 +170,26 @@ lbib_status sim_upload(lbib_sim *s) {
         s->d.obj = s->d_obj;
         s->d.fext = s->d_fext;
         s->d.nobj = nobj;
+        // repulsion buffers: boxes [nobj][8], a pair list of 32 per object
+        const bool rep = s->rep_obj[0] > 0.0 && s->rep_obj[2] > 0.0 && nobj >= 2;
+        if (rep && nobj > s->rep_cap_obj) {
+            const int cap_obj = std::max(nobj, 2 * s->rep_cap_obj);
+            if (s->rep_mem) cudaFree(s->rep_mem);
+            s->rep_mem = nullptr;
+            s->rep_cap_obj = 0;
+            s->rep_bytes = 0;
+            const size_t pairs = 32 * (size_t)cap_obj + 1024;
+            const size_t bytes = align_up((size_t)cap_obj * 8 * sizeof(float), 256) + pairs * sizeof(int4) + 256;
+            LBIB_CUDA(s, cudaMalloc(&s->rep_mem, bytes), "repulsion buffers");
+            s->rep_cap_obj = cap_obj;
+            s->rep_bytes = bytes;
+            char *b = (char *)s->rep_mem;
+            s->d.aabb = (float *)b;
+            s->d.pairs = (int4 *)(b + align_up((size_t)cap_obj * 8 * sizeof(float), 256));
+            s->d.npairs = (unsigned *)(b + align_up((size_t)cap_obj * 8 * sizeof(float), 256) + pairs * sizeof(int4));
+            s->d.pair_cap = (int)pairs;
+        }
+        s->d.rep_on = rep ? 1 : 0;
         s->tables_dirty = false;
         s->fel_valid = false;
     }
@@ -370,6 +394,7 @@ void lbib_destroy(lbib_sim *s) {
     for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : s->prof_aux) cudaEventDestroy(e);
     if (s->dnodes) cudaFree(s->dnodes);
+    if (s->rep_mem) cudaFree(s->rep_mem);
     if (s->fluid_mem) cudaFree(s->fluid_mem);
     delete s;
 }
@@ -538,6 +563,34 @@ lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3
     return LBIB_OK;
 }
 
+lbib_status lbib_set_repulsion(lbib_sim *s, const double object[3], const double wall[3]) {
+    LBIB_GUARD(s);
+    if (!object || !wall) return fail(s, LBIB_ERR_ARG, "null parameters");
+    for (const double *p : {object, wall}) {
+        if (!(p[0] >= 0.0) || !(p[2] >= 0.0) || (p[0] > 0.0 && !(p[1] > 0.0)))
+            return fail(s, LBIB_ERR_ARG, "repulsion needs a >= 0, n > 0, cutoff >= 0");
+    }
+    // the nearest periodic image must be the only one within the cutoff
+    const double half = 0.5 * std::min(s->p.nx, s->p.nz);
+    if (object[2] >= half || (!s->p.walls_y && object[2] >= 0.5 * s->p.ny))
+        return fail(s, LBIB_ERR_ARG, "repulsion cutoff must be below half the periodic box");
+    for (int k = 0; k < 3; ++k) {
+        s->rep_obj[k] = object[k];
+        s->rep_wall[k] = wall[k];
+    }
+    SimDev &d = s->d;
+    d.rep_a = (float)object[0];
+    d.rep_n = (float)object[1];
+    d.rep_rc = (float)object[2];
+    d.rep_wa = (float)wall[0];
+    d.rep_wn = (float)wall[1];
+    d.rep_wrc = (float)wall[2];
+    d.rep_wall_on = (s->p.walls_y && wall[0] > 0.0 && wall[2] > 0.0) ? 1 : 0;
+    s->tables_dirty = true;  // (re)sizes the pair buffers and sets rep_on
+    s->fel_valid = false;
+    return LBIB_OK;
+}
+
 lbib_status lbib_object_set_force(lbib_sim *s, int oid, const double f[3]) {
     LBIB_GUARD(s);
     if (oid < 0 || oid >= (int)s->objs.size()) return fail(s, LBIB_ERR_ID, "unknown object id");
@@ -603,6 +656,7 @@ static lbib_status launch_membrane_timed(lbib_sim *s, cudaStream_t st) {
         LBIB_CUDA(s, cudaEventRecord(ev[0], st), "profile event");
     }
     LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, st), "membrane forces");
+    LBIB_CUDA(s, launch_repulsion(s->d, s->max_nodes, st), "repulsion");
     if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], st), "profile event");
     return LBIB_OK;
 }
@@ -871,7 +925,7 @@ lbib_status lbib_info(const lbib_sim *s, int64_t out[8]) {
     out[2] = s->nn_total;
     out[3] = s->d.nf;
     out[4] = s->t;
-    out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes);
+    out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes + s->rep_bytes);
     out[6] = s->p.precision;
     out[7] = 0;
     return LBIB_OK;

@@ -54,6 +54,135 @@ cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ repulsion
+// Object-object soft-sphere repulsion, in two launches after the membrane
+// kernel (which wrote each object's bounding box):
+//   k_rep_pairs   one thread per object pair (i < j): the periodic image of
+//                 j nearest to i (minimum image of the box centres; the box
+//                 is taken larger than twice an object plus the cutoff), and
+//                 whether the boxes widened by the cutoff overlap; close
+//                 pairs go to a list
+//   k_rep_forces  one block per listed pair: j's nodes (shifted to the
+//                 image) are staged in shared memory as hi + lo pairs; each
+//                 thread takes nodes of i inside j's widened box and tests
+//                 all of j's nodes; the pair force goes to i's node directly
+//                 and to j's node through a shared-memory sum, both added
+//                 to Fel with global atomics.
+// Separations are formed as (hi_i - hi_j) + (lo_i - lo_j), exact in the
+// leading part for nearby nodes, so the force does not lose digits at
+// large coordinates.
+
+__device__ __forceinline__ int image_shift(float ci, float cj, int L) {
+    return (int)rintf((ci - cj) / (float)L);  // j + shift * L is the image nearest to i
+}
+
+__global__ void __launch_bounds__(256) k_rep_pairs(SimDev s) {
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j <= i || j >= s.nobj) return;
+    const float *A = s.aabb + 8 * i, *B = s.aabb + 8 * j;
+    const int L[3] = {s.nx, s.ny, s.nz};
+    int k3[3];
+    bool close = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool periodic = k != 1 || !s.walls;
+        k3[k] = periodic ? image_shift(0.5f * (A[k] + A[3 + k]), 0.5f * (B[k] + B[3 + k]), L[k]) : 0;
+        const float sh = (float)(k3[k] * L[k]);
+        close = close && (B[k] + sh < A[3 + k] + s.rep_rc) && (A[k] < B[3 + k] + sh + s.rep_rc);
+    }
+    if (!close) return;
+    const unsigned slot = atomicAdd(s.npairs, 1u);
+    if (slot < (unsigned)s.pair_cap)
+        s.pairs[slot] = make_int4(i | (j << 16), k3[0], k3[1], k3[2]);  // nobj <= 65535
+    else
+        atomicOr(s.status, ST_PAIRS);
+}
+
+extern __shared__ float rep_smem[];
+
+__global__ void __launch_bounds__(256) k_rep_forces(SimDev s) {
+    const unsigned np = min(*s.npairs, (unsigned)s.pair_cap);
+    const int NN = s.nn_total;
+    const float rc2 = s.rep_rc * s.rep_rc;
+    for (unsigned p = blockIdx.x; p < np; p += gridDim.x) {
+        const int4 pr = s.pairs[p];
+        const int oi = pr.x & 0xffff, oj = (int)((unsigned)pr.x >> 16);
+        const ObjDev A = s.obj[oi], B = s.obj[oj];
+        const float sh[3] = {(float)(pr.y * s.nx), (float)(pr.z * s.ny), (float)(pr.w * s.nz)};
+        float *bh = rep_smem, *bl = bh + 3 * B.nn, *bf = bl + 3 * B.nn;
+        for (int q = threadIdx.x; q < B.nn; q += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                // (hi + shift) as an unevaluated pair: the shift is an integer
+                const df t = two_sum(s.Xh[k * NN + B.first + q], sh[k]);
+                bh[3 * q + k] = t.hi;
+                bl[3 * q + k] = t.lo + s.Xl[k * NN + B.first + q];
+                bf[3 * q + k] = 0.f;
+            }
+        __syncthreads();
+        const float *bb = s.aabb + 8 * oj;
+        for (int a = threadIdx.x; a < A.nn; a += blockDim.x) {
+            float xh[3], xl[3];
+            bool inside = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                xh[k] = s.Xh[k * NN + A.first + a];
+                xl[k] = s.Xl[k * NN + A.first + a];
+                inside = inside && xh[k] > bb[k] + sh[k] - s.rep_rc - 1e-3f && xh[k] < bb[3 + k] + sh[k] + s.rep_rc + 1e-3f;
+            }
+            if (!inside) continue;
+            float F[3] = {0.f, 0.f, 0.f};
+            for (int q = 0; q < B.nn; ++q) {
+                const float dx = (xh[0] - bh[3 * q]) + (xl[0] - bl[3 * q]);
+                const float dy = (xh[1] - bh[3 * q + 1]) + (xl[1] - bl[3 * q + 1]);
+                const float dz = (xh[2] - bh[3 * q + 2]) + (xl[2] - bl[3 * q + 2]);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < rc2 && r2 > 0.f) {
+                    const float rr = sqrtf(r2);
+                    const float f = soft_force(s.rep_a, s.rep_n, rr) / rr;
+                    F[0] += f * dx;
+                    F[1] += f * dy;
+                    F[2] += f * dz;
+                    atomicAdd(bf + 3 * q, -f * dx);
+                    atomicAdd(bf + 3 * q + 1, -f * dy);
+                    atomicAdd(bf + 3 * q + 2, -f * dz);
+                }
+            }
+            if (F[0] != 0.f || F[1] != 0.f || F[2] != 0.f)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) atomicAdd(s.Fel + k * NN + A.first + a, F[k]);
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < B.nn; q += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (bf[3 * q + k] != 0.f) atomicAdd(s.Fel + k * NN + B.first + q, bf[3 * q + k]);
+        __syncthreads();  // shared memory is restaged for the next pair
+    }
+}
+
+cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st) {
+    if (!s.rep_on || s.nobj < 2) return cudaSuccess;
+    if (s.nobj > 65535) return cudaErrorInvalidValue;  // grid rows and the pair encoding
+    cudaError_t e = cudaMemsetAsync(s.npairs, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    k_rep_pairs<<<dim3((s.nobj + 255) / 256, s.nobj), 256, 0, st>>>(s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = (size_t)9 * max_nodes * sizeof(float);
+    static size_t configured = 0;
+    if (smem > configured) {
+        e = cudaFuncSetAttribute(k_rep_forces, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_rep_forces<<<2 * sms, 256, smem, st>>>(s);
+    return cudaGetLastError();
+}
+
 // Marks the cells around every node as active (after the mask was cleared).
 __global__ void k_mark_all(SimDev s) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;

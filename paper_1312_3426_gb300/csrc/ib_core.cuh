@@ -354,8 +354,57 @@ __device__ __forceinline__ int share_lo32(int n, int r, int C) {
     return r >= C ? n : (int)((((long long)n * r) / C) & ~31LL);
 }
 
+// Soft-sphere force magnitude a n r^-(n+1) (the repulsion reading; see
+// lbib.h lbib_set_repulsion).
+__device__ __forceinline__ float soft_force(float a, float n, float r) { return a * n * powf(r, -(n + 1.0f)); }
+
+// Wall term of the repulsion for a node at height y (hi + lo): pushed away
+// from the planes y = 1 and y = ny - 1 when closer than the cutoff.
+__device__ __forceinline__ float wall_force(const SimDev &s, float yh, float yl) {
+    const float dlo = (yh - 1.0f) + yl;
+    const float dhi = ((float)(s.ny - 1) - yh) - yl;
+    float f = 0.f;
+    if (dlo < s.rep_wrc) f += soft_force(s.rep_wa, s.rep_wn, fmaxf(dlo, 1e-3f));
+    if (dhi < s.rep_wrc) f -= soft_force(s.rep_wa, s.rep_wn, fmaxf(dhi, 1e-3f));
+    return f;
+}
+
+// Bounding box of object o from its staged relative positions plus the
+// first node's position (FP32: a broad-phase filter, widened by the
+// cutoff where it is used).  All threads of the block call it.
+__device__ __forceinline__ void object_box(const SimDev &s, int o, const Stage &P, int nn, int f0) {
+    float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+        const float4 h = P.hi[p];
+        mn[0] = fminf(mn[0], h.x), mn[1] = fminf(mn[1], h.y), mn[2] = fminf(mn[2], h.z);
+        mx[0] = fmaxf(mx[0], h.x), mx[1] = fmaxf(mx[1], h.y), mx[2] = fmaxf(mx[2], h.z);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], off));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], off));
+        }
+    __shared__ float box_part[6][IB_THREADS / 32];
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            box_part[k][threadIdx.x >> 5] = mn[k];
+            box_part[3 + k][threadIdx.x >> 5] = mx[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        float v = box_part[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = k < 3 ? fminf(v, box_part[k][w]) : fmaxf(v, box_part[k][w]);
+        const int c = k % 3;
+        s.aabb[8 * o + k] = v + s.Xh[c * s.nn_total + f0];
+    }
+}
+
 // The membrane part of object o by the calling cluster (all C blocks call
-// it): writes the membrane force of each of its nodes to s.Fel.
+// it): writes the membrane force of each of its nodes to s.Fel (plus the
+// wall repulsion, when set).
 __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *sh) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
@@ -385,6 +434,9 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
         Fz[p] = 0.f;
     }
     __syncthreads();
+
+    // 1b. bounding box of the object's nodes (broad phase of the repulsion)
+    if (s.rep_on && r == 0) object_box(s, o, P, nn, f0);
 
     // 2. this block's share of the area and volume sums
     df area{0.f, 0.f}, vol{0.f, 0.f};
@@ -456,6 +508,7 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
             const float *Fj = cl.map_shared_rank(sh, j) + 8 * nn;
             Fp = Fp + mk(Fj[p], Fj[nn + p], Fj[2 * nn + p]);
         }
+        if (s.rep_wall_on) Fp.y += wall_force(s, s.Xh[NN + f0 + p], s.Xl[NN + f0 + p]);
         s.Fel[f0 + p] = Fp.x;
         s.Fel[NN + f0 + p] = Fp.y;
         s.Fel[2 * NN + f0 + p] = Fp.z;

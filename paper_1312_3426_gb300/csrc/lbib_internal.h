@@ -65,6 +65,7 @@ enum : uint32_t {
     ST_UNSTABLE = 1u,     // NaN or |u|^2 > 0.09 in a fluid cell
     ST_NODE_NAN = 2u,     // non-finite node position
     ST_TIMEOUT = 4u,      // a bounded device-side wait gave up
+    ST_PAIRS = 8u,        // more close object pairs than the repulsion pair list holds
 };
 
 // Element lists of one template (device), all node ids local to an object:
@@ -91,8 +92,6 @@ struct ObjDev {
     float inv_mass;
 };
 
-// Everything a kernel needs to know about one simulation (POD, passed by
-// value to single-simulation kernels and stored in an array for batches).
 // Division by a fixed divisor d >= 1 of any 32-bit unsigned n with one
 // multiply-high (Granlund and Montgomery, "Division by invariant integers
 // using multiplication", PLDI 1994): l = ceil(log2 d),
@@ -115,6 +114,8 @@ struct FastDiv {
 #endif
 };
 
+// Everything a kernel needs to know about one simulation (POD, passed by
+// value to single-simulation kernels and stored in an array for batches).
 struct SimDev {
     int nx, ny, nz, walls;
     FastDiv div_nx, div_nyf;  // cell index -> (x, row), row -> (y, z)
@@ -137,6 +138,14 @@ struct SimDev {
     const TplDev *tpl;
     uint32_t *status;
     double *dropped;          // [3]
+    // soft-sphere repulsion (a, n, cutoff): object-object and object-wall
+    float rep_a, rep_n, rep_rc;
+    float rep_wa, rep_wn, rep_wrc;
+    int rep_on, rep_wall_on;
+    float *aabb;              // [nobj][8]: min x,y,z, max x,y,z of each object's nodes
+    int4 *pairs;              // close object pairs (i, j, periodic image code, 0)
+    unsigned *npairs;
+    int pair_cap;
 };
 
 // ---- launchers (fluid.cu) -------------------------------------------------
@@ -161,6 +170,9 @@ cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int
 // memory); coupling part: one thread per node
 cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, cudaStream_t st);
 cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st);
+// object-object repulsion added to Fel (after the membrane kernel, which
+// also writes the object bounding boxes); max_nodes sizes shared memory
+cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st);
 // oid >= 0: one object into out[14]; oid < 0: every object into out[nobj][14]
 cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st);
 cudaError_t launch_analyze(const SimDev &s, int oid, double *out, cudaStream_t st);

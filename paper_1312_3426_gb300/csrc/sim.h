@@ -57,6 +57,12 @@ struct lbib_sim {
     bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
 
+    double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects
+    double rep_wall[3] = {0, 1, 0};     // and against the walls
+    void *rep_mem = nullptr;            // object boxes, pair list, pair count
+    int rep_cap_obj = 0;                // objects the buffers hold
+    size_t rep_bytes = 0;
+
     bool prof_on = false;        // per-phase CUDA-event timing
     std::vector<cudaEvent_t> prof_ev;   // 3 per step on `stream`
     std::vector<cudaEvent_t> prof_aux;  // 2 per membrane launch on `aux`

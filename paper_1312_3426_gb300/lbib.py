@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
                                  C.c_int]),
         "lbib_object_add": (st, [P, C.c_int, C.c_int, P, P, C.c_double]),
         "lbib_object_set_force": (st, [P, C.c_int, P]),
+        "lbib_set_repulsion": (st, [P, P, P]),
         "lbib_object_set_nodes": (st, [P, C.c_int, P, C.c_int]),
         "lbib_object_set_velocities": (st, [P, C.c_int, P, C.c_int]),
         "lbib_fluid_init": (st, [P]),
@@ -310,6 +311,12 @@ def lbib_profile_read(h):
                 membrane_ms=out[4], membrane_launches=int(out[5]))
 
 
+def lbib_set_repulsion(h, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
+    a = _f64(obj, (3,))
+    b = _f64(wall, (3,))
+    _check(h, _lib.lbib_set_repulsion(h, _p(a), _p(b)))
+
+
 def lbib_fluid_mass_noalloc(h):
     out = np.zeros(1)
     _check(h, _lib.lbib_fluid_mass_noalloc(h, _p(out)))
@@ -423,6 +430,9 @@ class Sim:
             oid = s.object_add(o.tid, o.origin, o.rotate, o.mass)
             if any(o.force):
                 s.object_set_force(oid, o.force)
+        rep = getattr(scene, "repulsion", None)
+        if rep is not None:
+            lbib_set_repulsion(s.h, *rep)
         if init:
             s.fluid_init()
         return s

@@ -41,3 +41,13 @@ def test_drag_per_lattice_step_is_friction_times_time_step():
 def test_node_mass_default_is_unit():
     g = _golden()
     assert scenes.Obj(0, (0, 0, 0)).mass == g["node_mass"][0]
+
+
+def test_repulsion_in_lattice_units_is_the_papers_times_time_step_squared():
+    g = _golden()
+    dt2 = g["md_time_step"][0] ** 2
+    (oa, on, orc), (wa, wn, wrc) = scenes.PAPER_REPULSION
+    assert oa == pytest.approx(g["soft_obj_a"][0] * dt2) and on == g["soft_obj_n"][0]
+    assert orc == g["soft_obj_cutoff"][0]
+    assert wa == pytest.approx(g["soft_wall_a"][0] * dt2) and wn == g["soft_wall_n"][0]
+    assert wrc == g["soft_wall_cutoff"][0]

@@ -396,3 +396,70 @@ def test_unstable_fluid_is_reported_and_sticky():
     with pytest.raises(lbib.LbibError) as e:
         g.step(1)
     assert e.value.status == -5
+
+
+# ------------------------------------------------------------- soft-sphere repulsion (Sec. 6 interactions)
+
+def _probe_scene(centres, nx=24, ny=18, nz=18, friction=0.0, moduli=None, radius=2.0):
+    s = scenes.Scene("rep", nx, ny, nz, body_force=(0.0, 0.0, 0.0), friction=friction)
+    n1, t1 = mesh.icosphere(1)  # has vertices on the coordinate axes
+    s.templates.append(scenes.Template(n1, t1, (radius,) * 3, **(moduli or {})))
+    for c in centres:
+        s.objects.append(scenes.Obj(0, c))
+    return s
+
+
+@pytest.mark.parametrize("case", ["pair", "periodic", "wall"])
+def test_repulsion_forces_match_oracle(case):
+    """xi = 0, moduli 0, nodes at rest: one step gives v = F_rep / m."""
+    R = 2.0
+    if case == "pair":      # +x vertex of A and -x vertex of B 0.2 apart
+        sc = _probe_scene([(8.0, 9.0, 9.0), (8.0 + 2 * R + 0.2, 9.0, 9.0)])
+    elif case == "periodic":  # the same through the face x = 0
+        sc = _probe_scene([(R + 0.1, 9.0, 9.0), (24.0 - R - 0.1, 9.0, 9.0)])
+    else:                   # lowest vertex 0.2 above the wall plane y = 1
+        sc = _probe_scene([(8.0, 1.0 + R + 0.2, 9.0)])
+    sc.repulsion = ((5e-5, 2.0, 0.5), (1e-6, 1.2, 0.5))
+    o = oracle.Oracle.from_scene(sc)
+    F = o.repulsion_forces()
+    assert np.abs(F).max() > 0
+    g = lbib.Sim.from_scene(sc)
+    g.step(1)
+    _, v = g.read_nodes(-1)
+    assert np.abs(v - F).max() <= 1e-5 * np.abs(F).max(), np.abs(v - F).max() / np.abs(F).max()
+    if case != "wall":
+        assert np.abs(v.sum(0)).max() <= 1e-6 * np.abs(F).max()  # third law (FP32 sums)
+
+
+def test_repulsion_dynamics_match_oracle():
+    """Two elastic objects driven head-on into each other through the
+    fluid: the repulsion stops them as in the oracle.  Pressed head-on the
+    pair sits in an unstable equilibrium (it can slip sideways), where any
+    rounding difference grows by ~e^(0.07 t), so the comparison ends 30
+    steps after the first contact (step ~100)."""
+    sc = _probe_scene([(8.0, 9.0, 9.0), (8.0 + 2 * 2.5 + 0.55, 9.0, 9.0)], friction=0.05,
+                      moduli=scenes.PAPER_MODULI, radius=2.5)
+    sc.objects[0].force = (2e-4, 0.0, 0.0)
+    sc.objects[1].force = (-2e-4, 0.0, 0.0)
+    sc.repulsion = ((5e-5, 2.0, 0.5), (1e-6, 1.2, 0.5))
+    o, g = run_pair(sc, 130)
+    assert np.abs(o.repulsion_forces()).max() > 1e-3  # in contact
+    # the only flow is the one the objects drive, and at contact a node
+    # position difference dx changes the contact force by (n+1) dx / r
+    # relative (about 10x at r ~ 0.2): the fluid bar is widened by that
+    err_u, err_x = rel_l2(g.velocity(), o.velocity(), sc), nodes_maxabs(g, o, 2)
+    assert err_u <= 1e-4 and err_x <= node_tol(sc, o), (err_u, err_x, node_tol(sc, o))
+
+
+def test_wall_repulsion_holds_an_object_like_the_oracle():
+    """An object pushed against the lower wall comes to rest on the wall
+    term (a stable contact), as in the oracle."""
+    sc = _probe_scene([(12.0, 1.0 + 2.5 + 0.4, 9.0)], friction=0.05, moduli=scenes.PAPER_MODULI, radius=2.5)
+    sc.objects[0].force = (0.0, -1e-4, 0.0)
+    sc.repulsion = ((5e-5, 2.0, 0.5), (1e-6, 1.2, 0.5))
+    o, g = run_pair(sc, 300)
+    x, _ = o.read_nodes(0)
+    assert x[:, 1].min() > 1.0 and np.abs(o.repulsion_forces()).max() > 1e-5  # held above the plane
+    # as above, with the wall term's (n+1)/d = 92 at the final gap d = 0.024
+    err_u, err_x = rel_l2(g.velocity(), o.velocity(), sc), nodes_maxabs(g, o, 1)
+    assert err_u <= 1e-3 and err_x <= node_tol(sc, o), (err_u, err_x, node_tol(sc, o))

@@ -36,6 +36,14 @@ from . import mesh as _mesh
 
 PAPER_MODULI = dict(ks=0.1, kb=0.03, kal=0.1, kag=0.4, kv=1.0)
 
+# The soft-sphere interactions of the paper's blood-cell example (Sec. 6):
+# object-object (a 0.005, n 2, cutoff 0.3) and object-wall (a 0.0001, n 1.2,
+# cutoff 0.1), set at an MD time step of 0.1 with the lattice spacing as the
+# length unit.  A force integrated over one lattice step (the unit time step
+# here) scales with the time step squared, so in lattice units a becomes
+# a x 0.1^2; n and the cutoffs are lengths' exponents and lengths and stay.
+PAPER_REPULSION = ((0.005 * 0.1 ** 2, 2.0, 0.3), (0.0001 * 0.1 ** 2, 1.2, 0.1))
+
 
 @dataclass
 class Template:
