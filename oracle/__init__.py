@@ -68,6 +68,7 @@ def _load():
         "oracle_step": (None, [P, C.c_int]),
         "oracle_step_nodes_only": (None, [P, C.c_int]),
         "oracle_set_repulsion": (C.c_int, [P, dp, dp]),
+        "oracle_set_inlet": (C.c_int, [P, ip, dp]),
         "oracle_repulsion_forces": (None, [P, dp]),
         "oracle_read_velocity": (None, [P, dp]),
         "oracle_set_velocity": (None, [P, dp]),
@@ -129,6 +130,9 @@ class Oracle:
         rep = getattr(scene, "repulsion", None)
         if rep is not None:
             o.set_repulsion(*rep)
+        inlet = getattr(scene, "inlet", None)
+        if inlet is not None:
+            o.set_inlet(*inlet)
         o.fluid_init()
         return o
 
@@ -206,6 +210,11 @@ class Oracle:
                                             np.ascontiguousarray(wall, dtype=np.float64))
         if rc != 0:
             raise ValueError("invalid repulsion parameters")
+
+    def set_inlet(self, box, u):
+        """Velocity inlet over cells box = (x0, x1, y0, y1, z0, z1) (half-open)."""
+        self._lib.oracle_set_inlet(self._h, np.ascontiguousarray(box, dtype=np.int32),
+                                   np.ascontiguousarray(u, dtype=np.float64))
 
     def n_nodes(self):
         return sum(self._lib.oracle_object_nodes(self._h, o) for o in range(self.n_objects))

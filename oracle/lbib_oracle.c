@@ -75,6 +75,8 @@ typedef struct {
 typedef struct osim {
     int nx, ny, nz, walls;
     osoft rep_obj, rep_wall;  /* object-object and object-wall repulsion (a = 0: off) */
+    int in_box[6];            /* velocity inlet cells x0..x1-1, y0..y1-1, z0..z1-1 (empty: off) */
+    double in_u[3];           /* prescribed velocity of the inlet */
     double tau, rho0, g[3], xi;
     long ncell;
     double *f, *fpost;        /* [ncell][NQ] */
@@ -734,14 +736,49 @@ void oracle_repulsion_forces(const osim *s, double *F)
     repulsion(s, F);
 }
 
-/* One full step, in the order: object measures and elastic forces (Sec. 4)
- * plus the repulsion (Sec. 6 interactions, when set), interpolation, drag,
+/* ------------------------------------------------------- inlet */
+
+/* Velocity inlet (Sec. 6 example: before every integration step the fluid
+ * velocity of the nodes of the inflow plane is set with "lbnode ... set u").
+ * Reading: setting the velocity of a node replaces its populations by the
+ * equilibrium at the node's own density and the prescribed velocity,
+ * f_i = w_i rho (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u). */
+int oracle_set_inlet(osim *s, const int *box, const double *u)
+{
+    for (int k = 0; k < 6; ++k) s->in_box[k] = box[k];
+    for (int k = 0; k < 3; ++k) s->in_u[k] = u[k];
+    return 0;
+}
+
+static void apply_inlet(osim *s)
+{
+    const int *b = s->in_box;
+    const double uu = dot3(s->in_u, s->in_u);
+    for (int z = b[4]; z < b[5]; ++z)
+        for (int y = b[2]; y < b[3]; ++y)
+            for (int x = b[0]; x < b[1]; ++x) {
+                if (x < 0 || x >= s->nx || y < 0 || y >= s->ny || z < 0 || z >= s->nz || is_solid_row(s, y)) continue;
+                double *f = s->f + NQ * cell_index(s, x, y, z);
+                double rho = 0.0;
+                for (int q = 0; q < NQ; ++q) rho += f[q];
+                for (int q = 0; q < NQ; ++q) {
+                    const double e[3] = {s->E[q][0], s->E[q][1], s->E[q][2]};
+                    const double eu = dot3(e, s->in_u);
+                    f[q] = s->W[q] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+                }
+            }
+}
+
+/* One full step, in the order: the velocity inlet (when set), object
+ * measures and elastic forces (Sec. 4) plus the repulsion (Sec. 6
+ * interactions, when set), interpolation, drag,
  * spreading and Newton update of the nodes (Sec. 2),
  * then collision and propagation of the fluid (Eq. lbequation) under the
  * body force plus the spread force. */
 void oracle_step(osim *s, int nsteps)
 {
     for (int it = 0; it < nsteps; ++it) {
+        apply_inlet(s);
         memset(s->G, 0, sizeof(double) * 3 * s->ncell);
         if (s->nnode) memset(s->Fel, 0, sizeof(double) * 3 * s->nnode);
         for (int o = 0; o < s->nobj; ++o) {

@@ -85,6 +85,8 @@ class Scene:
     # soft-sphere repulsion ((a, n, cutoff) object-object, (a, n, cutoff)
     # object-wall), or None for none
     repulsion: tuple = None
+    # velocity inlet ((x0, x1, y0, y1, z0, z1) cell box, (ux, uy, uz)), or None
+    inlet: tuple = None
     templates: list = field(default_factory=list)
     objects: list = field(default_factory=list)
 
