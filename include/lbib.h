@@ -160,6 +160,16 @@ LBIB_API lbib_status lbib_object_add(lbib_sim *sim, int oid, int tid, const doub
  * At most 32 close object pairs per object (sticky LBIB_ERR_NOMEM beyond). */
 LBIB_API lbib_status lbib_set_repulsion(lbib_sim *sim, const double object[3], const double wall[3]);
 
+/* Velocity inlet (the inflow of the Sec. 6 example, which sets the fluid
+ * velocity of a plane of nodes before every step): at the start of every
+ * step the populations of the cells x in [box[0], box[1]), y in
+ * [box[2], box[3]) (lattice rows, wall rows included and skipped), z in
+ * [box[4], box[5]) are replaced by the equilibrium at the cell's own
+ * density and velocity u[3], then collide as usual.  The box is clipped to
+ * the lattice; an empty box switches the inlet off (the default).
+ * LBIB_ERR_ARG for |u| >= 0.3. */
+LBIB_API lbib_status lbib_set_inlet(lbib_sim *sim, const int32_t box[6], const double u[3]);
+
 /* External force on every node of an object (Sec. 5, object customization). */
 LBIB_API lbib_status lbib_object_set_force(lbib_sim *sim, int oid, const double f[3]);
 

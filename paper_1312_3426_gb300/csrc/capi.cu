@@ -563,6 +563,24 @@ lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3
     return LBIB_OK;
 }
 
+lbib_status lbib_set_inlet(lbib_sim *s, const int32_t box[6], const double u[3]) {
+    LBIB_GUARD(s);
+    if (!box || !u) return fail(s, LBIB_ERR_ARG, "null parameters");
+    const int n[3] = {s->p.nx, s->p.ny, s->p.nz};
+    int b[6];
+    for (int k = 0; k < 3; ++k) {
+        b[2 * k] = std::max(0, std::min(box[2 * k], n[k]));
+        b[2 * k + 1] = std::max(b[2 * k], std::min(box[2 * k + 1], n[k]));
+    }
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if (!(usq < 0.09)) return fail(s, LBIB_ERR_ARG, "inlet speed must be below 0.3");
+    SimDev &d = s->d;
+    for (int k = 0; k < 6; ++k) d.in_box[k] = b[k];
+    for (int k = 0; k < 3; ++k) d.in_u[k] = (float)u[k];
+    d.in_on = (b[0] < b[1] && b[2] < b[3] && b[4] < b[5]) ? 1 : 0;
+    return LBIB_OK;
+}
+
 lbib_status lbib_set_repulsion(lbib_sim *s, const double object[3], const double wall[3]) {
     LBIB_GUARD(s);
     if (!object || !wall) return fail(s, LBIB_ERR_ARG, "null parameters");

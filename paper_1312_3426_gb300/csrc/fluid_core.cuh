@@ -231,6 +231,47 @@ __device__ __forceinline__ CollK make_collk(const SimDev &s) {
     return k;
 }
 
+// Velocity inlet (the inflow plane of the Sec. 6 example, whose velocity is
+// set before every step): the populations pulled into an inlet cell are
+// replaced by the equilibrium at the cell's own density and the prescribed
+// velocity, w (drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)) in deviation
+// form, before the collision.  h holds raw numbers (times 2^s).
+template <int Q>
+__device__ __forceinline__ float inlet_eq(float drho, float rho, float usq, const float *u, float sc) {
+    const float eu = edot<Q>(u[0], u[1], u[2]);
+    return (float)d3q19_w(Q) * sc * (drho + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq));
+}
+
+__device__ __forceinline__ void inlet_cell(const SimDev &s, int x, int yl, int z, float (&h)[NQ]) {
+    const int *b = s.in_box;
+    if (x < b[0] || x >= b[1] || yl < b[2] || yl >= b[3] || z < b[4] || z >= b[5]) return;
+    float sr = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sr += h[q];
+    const float drho = sr * s.inv_scale, rho = s.rho0 + drho, sc = s.scale;
+    const float *u = s.in_u;
+    const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    h[0] = inlet_eq<0>(drho, rho, usq, u, sc);
+    h[1] = inlet_eq<1>(drho, rho, usq, u, sc);
+    h[2] = inlet_eq<2>(drho, rho, usq, u, sc);
+    h[3] = inlet_eq<3>(drho, rho, usq, u, sc);
+    h[4] = inlet_eq<4>(drho, rho, usq, u, sc);
+    h[5] = inlet_eq<5>(drho, rho, usq, u, sc);
+    h[6] = inlet_eq<6>(drho, rho, usq, u, sc);
+    h[7] = inlet_eq<7>(drho, rho, usq, u, sc);
+    h[8] = inlet_eq<8>(drho, rho, usq, u, sc);
+    h[9] = inlet_eq<9>(drho, rho, usq, u, sc);
+    h[10] = inlet_eq<10>(drho, rho, usq, u, sc);
+    h[11] = inlet_eq<11>(drho, rho, usq, u, sc);
+    h[12] = inlet_eq<12>(drho, rho, usq, u, sc);
+    h[13] = inlet_eq<13>(drho, rho, usq, u, sc);
+    h[14] = inlet_eq<14>(drho, rho, usq, u, sc);
+    h[15] = inlet_eq<15>(drho, rho, usq, u, sc);
+    h[16] = inlet_eq<16>(drho, rho, usq, u, sc);
+    h[17] = inlet_eq<17>(drho, rho, usq, u, sc);
+    h[18] = inlet_eq<18>(drho, rho, usq, u, sc);
+}
+
 template <typename T>
 __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, bool active, uint32_t step_seed) {
     static_assert(d3q19_opp(1) == 2 && d3q19_opp(17) == 18, "directions 2k-1, 2k must be opposite");
@@ -249,6 +290,8 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
     LBIB_PULL(7) LBIB_PULL(8) LBIB_PULL(9) LBIB_PULL(10) LBIB_PULL(11) LBIB_PULL(12) LBIB_PULL(13)
     LBIB_PULL(14) LBIB_PULL(15) LBIB_PULL(16) LBIB_PULL(17) LBIB_PULL(18)
 #undef LBIB_PULL
+
+    if (s.in_on) inlet_cell(s, (int)x, (int)y + s.walls, (int)z, h);
 
     float Gx = s.gx, Gy = s.gy, Gz = s.gz;
     if (active) {  // spread force of this step; clear the buffer of the next

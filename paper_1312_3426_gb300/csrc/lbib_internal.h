@@ -143,9 +143,14 @@ struct SimDev {
     float rep_wa, rep_wn, rep_wrc;
     int rep_on, rep_wall_on;
     float *aabb;              // [nobj][8]: min x,y,z, max x,y,z of each object's nodes
-    int4 *pairs;              // close object pairs (i, j, periodic image code, 0)
+    int4 *pairs;              // close object pairs (i | j << 16, image shift x, y, z)
     unsigned *npairs;
     int pair_cap;
+    // velocity inlet: cells x in [in_box[0], in_box[1]), y (lattice row, walls
+    // included) in [in_box[2], in_box[3]), z in [in_box[4], in_box[5])
+    int in_on;
+    int in_box[6];
+    float in_u[3];
 };
 
 // ---- launchers (fluid.cu) -------------------------------------------------

@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
         "lbib_object_add": (st, [P, C.c_int, C.c_int, P, P, C.c_double]),
         "lbib_object_set_force": (st, [P, C.c_int, P]),
         "lbib_set_repulsion": (st, [P, P, P]),
+        "lbib_set_inlet": (st, [P, P, P]),
         "lbib_object_set_nodes": (st, [P, C.c_int, P, C.c_int]),
         "lbib_object_set_velocities": (st, [P, C.c_int, P, C.c_int]),
         "lbib_fluid_init": (st, [P]),
@@ -317,6 +318,12 @@ def lbib_set_repulsion(h, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
     _check(h, _lib.lbib_set_repulsion(h, _p(a), _p(b)))
 
 
+def lbib_set_inlet(h, box, u):
+    b = np.ascontiguousarray(box, dtype=np.int32).reshape(6)
+    v = _f64(u, (3,))
+    _check(h, _lib.lbib_set_inlet(h, _p(b), _p(v)))
+
+
 def lbib_fluid_mass_noalloc(h):
     out = np.zeros(1)
     _check(h, _lib.lbib_fluid_mass_noalloc(h, _p(out)))
@@ -433,6 +440,9 @@ class Sim:
         rep = getattr(scene, "repulsion", None)
         if rep is not None:
             lbib_set_repulsion(s.h, *rep)
+        inlet = getattr(scene, "inlet", None)
+        if inlet is not None:
+            lbib_set_inlet(s.h, *inlet)
         if init:
             s.fluid_init()
         return s

@@ -463,3 +463,35 @@ def test_wall_repulsion_holds_an_object_like_the_oracle():
     # as above, with the wall term's (n+1)/d = 92 at the final gap d = 0.024
     err_u, err_x = rel_l2(g.velocity(), o.velocity(), sc), nodes_maxabs(g, o, 1)
     assert err_u <= 1e-3 and err_x <= node_tol(sc, o), (err_u, err_x, node_tol(sc, o))
+
+
+# ------------------------------------------------------------- velocity inlet (Sec. 6 inflow plane)
+
+def _inlet_scene(with_objects=True):
+    # a small copy of the example's set-up: walls in y, the inflow plane
+    # z = 1 set to u = (0, 0, 0.01) inside the walls, two cells downstream
+    s = scenes.Scene("inlet", 20, 14, 36, body_force=(0.0, 0.0, 0.0))
+    s.inlet = ((1, 19, 1, 13, 1, 2), (0.0, 0.0, 0.01))
+    if with_objects:
+        n2, t2 = mesh.biconcave(2)
+        s.templates.append(scenes.Template(n2, t2, (3.5, 3.5, 3.5), **scenes.PAPER_MODULI))
+        s.objects.append(scenes.Obj(0, (10.0, 7.0, 12.0), (1.5707963, 0.0, 0.0)))
+        s.objects.append(scenes.Obj(0, (10.5, 7.2, 22.0), (1.5707963, 0.3, 0.0)))
+    return s
+
+
+def test_velocity_inlet_matches_oracle():
+    sc = _inlet_scene()
+    o, g = run_pair(sc, 400)
+    u = g.velocity()
+    assert np.abs(u[:, 1, 1:13, 1:19] - np.array([0, 0, 0.01])[:, None, None]).max() < 1e-7
+    assert rel_l2(u, o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert np.abs(o.read_nodes(0)[0][:, 2].mean() - 12.0) > 0.05  # the cells were carried
+
+
+@pytest.mark.parametrize("prec,bound", [("f16s", 1e-3), ("bf16s", 2e-2)])
+def test_velocity_inlet_half_storage(prec, bound):
+    sc = _inlet_scene(with_objects=False)
+    o, g = run_pair(sc, 400, precision=prec, pop_scale_log2=12)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
