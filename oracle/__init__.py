@@ -69,6 +69,7 @@ def _load():
         "oracle_step_nodes_only": (None, [P, C.c_int]),
         "oracle_set_repulsion": (C.c_int, [P, dp, dp]),
         "oracle_set_inlet": (C.c_int, [P, ip, dp]),
+        "oracle_set_solid": (C.c_int, [P, P]),
         "oracle_repulsion_forces": (None, [P, dp]),
         "oracle_read_velocity": (None, [P, dp]),
         "oracle_set_velocity": (None, [P, dp]),
@@ -133,6 +134,9 @@ class Oracle:
         inlet = getattr(scene, "inlet", None)
         if inlet is not None:
             o.set_inlet(*inlet)
+        solid = getattr(scene, "solid", None)
+        if solid is not None:
+            o.set_solid(solid)
         o.fluid_init()
         return o
 
@@ -215,6 +219,15 @@ class Oracle:
         """Velocity inlet over cells box = (x0, x1, y0, y1, z0, z1) (half-open)."""
         self._lib.oracle_set_inlet(self._h, np.ascontiguousarray(box, dtype=np.int32),
                                    np.ascontiguousarray(u, dtype=np.float64))
+
+    def set_solid(self, mask):
+        """Obstacle cells from a [nz][ny][nx] boolean mask (None: none)."""
+        if mask is None:
+            self._lib.oracle_set_solid(self._h, None)
+            return
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(self.nz, self.ny, self.nx)
+        self._solid = m
+        self._lib.oracle_set_solid(self._h, m.ctypes.data_as(C.c_void_p))
 
     def n_nodes(self):
         return sum(self._lib.oracle_object_nodes(self._h, o) for o in range(self.n_objects))

@@ -76,6 +76,7 @@ typedef struct osim {
     int nx, ny, nz, walls;
     osoft rep_obj, rep_wall;  /* object-object and object-wall repulsion (a = 0: off) */
     int in_box[6];            /* velocity inlet cells x0..x1-1, y0..y1-1, z0..z1-1 (empty: off) */
+    unsigned char *solid;     /* [ncell] obstacle cells (NULL: none) */
     double in_u[3];           /* prescribed velocity of the inlet */
     double tau, rho0, g[3], xi;
     long ncell;
@@ -123,6 +124,13 @@ static long cell_index(const osim *s, int x, int y, int z)
 static int is_solid_row(const osim *s, int y)
 {
     return s->walls && (y <= 0 || y >= s->ny - 1);
+}
+
+/* Obstacle cells (the rhomboid obstacles of the Sec. 6 channel): solid like
+ * the wall rows, i.e. never updated and reflecting what streams into them. */
+static int is_solid_cell(const osim *s, long c, int y)
+{
+    return is_solid_row(s, y) || (s->solid && s->solid[c]);
 }
 
 static int wrap(int i, int n)
@@ -173,6 +181,7 @@ void oracle_destroy(osim *s)
     }
     free(s->tpl); free(s->obj); free(s->X); free(s->V); free(s->Fel);
     free(s->f); free(s->fpost); free(s->u); free(s->rho); free(s->G);
+    free(s->solid);
     free(s);
 }
 
@@ -555,6 +564,7 @@ static void corners(const osim *s, const double *X, long *idx, double *w)
             iy = wrap(iy, s->ny);
         }
         idx[c] = cell_index(s, ix, iy, iz);
+        if (s->solid && s->solid[idx[c]]) idx[c] = -1;
     }
 }
 
@@ -612,7 +622,7 @@ static void collide(osim *s)
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < s->ncell; ++c) {
         int y = (int)((c / s->nx) % s->ny);
-        if (is_solid_row(s, y)) continue;
+        if (is_solid_cell(s, c, y)) continue;
         const double *n = s->f + NQ * c;
         double *fp = s->fpost + NQ * c;
         double G[3], rho = 0.0, m[3] = {0.0, 0.0, 0.0}, u[3];
@@ -646,7 +656,7 @@ static void stream(osim *s)
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < s->ncell; ++c) {
         int x = (int)(c % s->nx), y = (int)((c / s->nx) % s->ny), z = (int)(c / ((long)s->nx * s->ny));
-        if (is_solid_row(s, y)) continue;
+        if (is_solid_cell(s, c, y)) continue;
         for (int q = 0; q < NQ; ++q) {
             int tx = wrap(x + s->E[q][0], s->nx), tz = wrap(z + s->E[q][2], s->nz);
             int ty = y + s->E[q][1];
@@ -655,7 +665,12 @@ static void stream(osim *s)
                 continue;
             }
             if (!s->walls) ty = wrap(ty, s->ny);
-            s->f[NQ * cell_index(s, tx, ty, tz) + q] = s->fpost[NQ * c + q];
+            const long t = cell_index(s, tx, ty, tz);
+            if (s->solid && s->solid[t]) {  /* halfway bounce-back at an obstacle */
+                s->f[NQ * c + s->OPP[q]] = s->fpost[NQ * c + q];
+                continue;
+            }
+            s->f[NQ * t + q] = s->fpost[NQ * c + q];
         }
     }
 }
@@ -664,8 +679,9 @@ static void stream(osim *s)
 void oracle_fluid_init(osim *s)
 {
     for (long c = 0; c < s->ncell; ++c) {
-        for (int q = 0; q < NQ; ++q) s->f[NQ * c + q] = s->W[q] * s->rho0;
-        s->rho[c] = s->rho0;
+        const int solid = s->solid && s->solid[c];
+        for (int q = 0; q < NQ; ++q) s->f[NQ * c + q] = solid ? 0.0 : s->W[q] * s->rho0;
+        s->rho[c] = solid ? 0.0 : s->rho0;
         s->u[3 * c] = s->u[3 * c + 1] = s->u[3 * c + 2] = 0.0;
     }
 }
@@ -736,6 +752,30 @@ void oracle_repulsion_forces(const osim *s, double *F)
     repulsion(s, F);
 }
 
+/* ------------------------------------------------------- obstacles */
+
+/* Marks obstacle cells from a [nz][ny][nx] byte mask (non-zero: solid);
+ * NULL removes every obstacle.  Solid cells hold no fluid: their
+ * populations and velocity are zero. */
+int oracle_set_solid(osim *s, const unsigned char *mask)
+{
+    if (!mask) {
+        free(s->solid);
+        s->solid = NULL;
+        return 0;
+    }
+    if (!s->solid) s->solid = (unsigned char *)calloc((size_t)s->ncell, 1);
+    for (long c = 0; c < s->ncell; ++c) {
+        s->solid[c] = mask[c] ? 1 : 0;
+        if (s->solid[c]) {
+            for (int q = 0; q < NQ; ++q) s->f[NQ * c + q] = s->fpost[NQ * c + q] = 0.0;
+            s->u[3 * c] = s->u[3 * c + 1] = s->u[3 * c + 2] = 0.0;
+            s->rho[c] = 0.0;
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------- inlet */
 
 /* Velocity inlet (Sec. 6 example: before every integration step the fluid
@@ -757,7 +797,8 @@ static void apply_inlet(osim *s)
     for (int z = b[4]; z < b[5]; ++z)
         for (int y = b[2]; y < b[3]; ++y)
             for (int x = b[0]; x < b[1]; ++x) {
-                if (x < 0 || x >= s->nx || y < 0 || y >= s->ny || z < 0 || z >= s->nz || is_solid_row(s, y)) continue;
+                if (x < 0 || x >= s->nx || y < 0 || y >= s->ny || z < 0 || z >= s->nz) continue;
+                if (is_solid_cell(s, cell_index(s, x, y, z), y)) continue;
                 double *f = s->f + NQ * cell_index(s, x, y, z);
                 double rho = 0.0;
                 for (int q = 0; q < NQ; ++q) rho += f[q];
@@ -856,7 +897,7 @@ void oracle_fluid_totals(const osim *s, double *out4)
     double m = 0.0, p[3] = {0.0, 0.0, 0.0};
     for (long c = 0; c < s->ncell; ++c) {
         int y = (int)((c / s->nx) % s->ny);
-        if (is_solid_row(s, y)) continue;
+        if (is_solid_cell(s, c, y)) continue;
         for (int q = 0; q < NQ; ++q) {
             m += s->f[NQ * c + q];
             for (int k = 0; k < 3; ++k) p[k] += s->f[NQ * c + q] * s->E[q][k];

@@ -87,6 +87,8 @@ class Scene:
     repulsion: tuple = None
     # velocity inlet ((x0, x1, y0, y1, z0, z1) cell box, (ux, uy, uz)), or None
     inlet: tuple = None
+    # obstacle cells: bool [nz][ny][nx] (see geometry.rhomboid_mask), or None
+    solid: object = None
     templates: list = field(default_factory=list)
     objects: list = field(default_factory=list)
 
