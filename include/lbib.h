@@ -160,6 +160,17 @@ LBIB_API lbib_status lbib_object_add(lbib_sim *sim, int oid, int tid, const doub
  * At most 32 close object pairs per object (sticky LBIB_ERR_NOMEM beyond). */
 LBIB_API lbib_status lbib_set_repulsion(lbib_sim *sim, const double object[3], const double wall[3]);
 
+/* Obstacle cells (the rhomboid obstacles of the Sec. 6 channel): mask
+ * [nz][ny][nx] bytes, non-zero = solid; n must be nx*ny*nz.  Entries in the
+ * wall rows are ignored.  Obstacle cells hold no fluid and are treated like
+ * the wall rows: a population streaming into one is reflected back into
+ * its own cell (halfway bounce-back), velocity interpolation sees u = 0
+ * there and force spread there is dropped (lbib_dropped_momentum).
+ * Read-outs give u = 0 and rho = 0 at obstacle cells, and populations with
+ * zero deviation; lbib_fluid_mass counts fluid cells only.  NULL removes
+ * every obstacle.  Must precede lbib_fluid_init (LBIB_ERR_STATE). */
+LBIB_API lbib_status lbib_set_solid(lbib_sim *sim, const uint8_t *mask, int64_t n);
+
 /* Velocity inlet (the inflow of the Sec. 6 example, which sets the fluid
  * velocity of a plane of nodes before every step): at the start of every
  * step the populations of the cells x in [box[0], box[1]), y in

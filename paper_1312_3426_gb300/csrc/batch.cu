@@ -37,15 +37,16 @@ constexpr int LBIB_BATCH_GRAPH_STEPS = 16;  // steps per captured graph
 
 extern __shared__ float batch_smem[];
 
-// One launch per storage type present in the batch (items grouped by type).
-template <typename T>
+// One launch per storage type and obstacle flag present in the batch (items
+// grouped by both).
+template <typename T, bool SOLID>
 __global__ void __launch_bounds__(FLUID_THREADS, 5)
     k_batch_fluid(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
                   const int2 *__restrict__ items) {
     const int2 it = items[blockIdx.x];  // (simulation, block of cells)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
-    fluid_block<T>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
+    fluid_block<T, SOLID>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
 }
 
 __global__ void __launch_bounds__(IB_THREADS, 3)
@@ -80,8 +81,8 @@ struct BatchPlan {
     int cluster = 0, device = -1;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
-    int2 *d_items = nullptr;  // fluid (FP32, FP16S, BF16S), then node, then membrane items
-    int n_flp[3] = {0, 0, 0};  // fluid items per storage type
+    int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
+    int n_flp[6] = {0, 0, 0, 0, 0, 0};  // fluid items per group 2 * precision + has-obstacles
     int n_fl = 0, n_nd = 0, n_mb = 0;
     int max_nodes = 0;
     cudaStream_t aux = nullptr;   // membrane kernel
@@ -142,19 +143,19 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_membrane, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
     }
-    std::vector<int2> flp[3], fl, nd, mb;
+    std::vector<int2> flp[6], fl, nd, mb;
     int max_nodes = 0;
     for (int i = 0; i < n; ++i) {
         const lbib_sim *s = sims[i];
         const int blocks = (s->d.nf + FLUID_THREADS - 1) / FLUID_THREADS;
-        for (int b = 0; b < blocks; ++b) flp[s->d.prec].push_back(make_int2(i, b));
+        for (int b = 0; b < blocks; ++b) flp[2 * s->d.prec + (s->d.solid ? 1 : 0)].push_back(make_int2(i, b));
         if (!s->objs.empty()) {
             for (int f = 0; f < s->nn_total; f += IB_THREADS) nd.push_back(make_int2(i, f));
             for (int o = 0; o < (int)s->objs.size(); ++o) mb.push_back(make_int2(i, o));
             max_nodes = std::max(max_nodes, s->max_nodes);
         }
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 6; ++k) {
         g_plan.n_flp[k] = (int)flp[k].size();
         fl.insert(fl.end(), flp[k].begin(), flp[k].end());
     }
@@ -230,13 +231,23 @@ static cudaError_t enqueue_steps(cudaStream_t st, int step_off, int k) {
             if ((e = launch_membrane_batch(g_plan.aux)) != cudaSuccess) break;
             if ((e = cudaEventRecord(g_plan.ev_membrane, g_plan.aux)) != cudaSuccess) break;
         }
-        const int2 *f16 = fl + g_plan.n_flp[0], *fb16 = f16 + g_plan.n_flp[1];
-        if (g_plan.n_flp[0]) k_batch_fluid<float><<<g_plan.n_flp[0], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, fl);
-        if (g_plan.n_flp[1])
-            k_batch_fluid<__half><<<g_plan.n_flp[1], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, f16);
-        if (g_plan.n_flp[2])
-            k_batch_fluid<__nv_bfloat16>
-                <<<g_plan.n_flp[2], FLUID_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, fb16);
+        {
+            const int2 *g = fl;
+            const int *n = g_plan.n_flp;
+            const SimDev *ds = g_plan.d_sims;
+            const long long *dt = g_plan.d_t;
+            if (n[0]) k_batch_fluid<float, false><<<n[0], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[0];
+            if (n[1]) k_batch_fluid<float, true><<<n[1], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[1];
+            if (n[2]) k_batch_fluid<__half, false><<<n[2], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[2];
+            if (n[3]) k_batch_fluid<__half, true><<<n[3], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[3];
+            if (n[4]) k_batch_fluid<__nv_bfloat16, false><<<n[4], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[4];
+            if (n[5]) k_batch_fluid<__nv_bfloat16, true><<<n[5], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (g_plan.n_nd) e = cudaStreamWaitEvent(st, g_plan.ev_membrane, 0);
     }

@@ -395,6 +395,7 @@ void lbib_destroy(lbib_sim *s) {
     for (cudaEvent_t e : s->prof_aux) cudaEventDestroy(e);
     if (s->dnodes) cudaFree(s->dnodes);
     if (s->rep_mem) cudaFree(s->rep_mem);
+    if (s->solid_mem) cudaFree(s->solid_mem);
     if (s->fluid_mem) cudaFree(s->fluid_mem);
     delete s;
 }
@@ -560,6 +561,39 @@ lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3
     s->nn_total += T.nn;
     s->host_newer = true;
     s->tables_dirty = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_solid(lbib_sim *s, const uint8_t *mask, int64_t n) {
+    LBIB_GUARD(s);
+    if (s->fluid_ready) return fail(s, LBIB_ERR_STATE, "obstacles must be set before lbib_fluid_init");
+    SimDev &d = s->d;
+    if (!mask) {
+        if (s->solid_mem) cudaFree(s->solid_mem);
+        s->solid_mem = nullptr;
+        d.solid = nullptr;
+        d.nsolid = 0;
+        return LBIB_OK;
+    }
+    const int64_t ncell = (int64_t)s->p.nx * s->p.ny * s->p.nz;
+    if (n != ncell) return fail(s, LBIB_ERR_ARG, "mask must cover the whole lattice [nz][ny][nx]");
+    std::vector<uint32_t> bits((size_t)d.nwords, 0u);
+    int count = 0;
+    for (int z = 0; z < d.nz; ++z)
+        for (int yf = 0; yf < d.nyf; ++yf)
+            for (int x = 0; x < d.nx; ++x) {
+                const int y = yf + d.walls;
+                if (!mask[((int64_t)z * d.ny + y) * d.nx + x]) continue;
+                const int f = x + d.nx * (yf + d.nyf * z);
+                bits[f >> 5] |= 1u << (f & 31);
+                ++count;
+            }
+    if (!s->solid_mem) LBIB_CUDA(s, cudaMalloc(&s->solid_mem, (size_t)d.nwords * 4), "obstacle mask");
+    LBIB_CUDA(s, cudaMemcpyAsync(s->solid_mem, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice, s->stream),
+              "obstacle mask");
+    LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "obstacle mask");
+    d.solid = s->solid_mem;
+    d.nsolid = count;
     return LBIB_OK;
 }
 
@@ -903,7 +937,7 @@ lbib_status lbib_fluid_mass(lbib_sim *s, double *mass) {
     cudaFreeAsync(acc, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "mass");
-    *mass = (double)s->d.nf * s->p.rho0 + dev;
+    *mass = (double)(s->d.nf - s->d.nsolid) * s->p.rho0 + dev;
     return LBIB_OK;
 }
 
@@ -932,7 +966,7 @@ lbib_status lbib_fluid_mass_noalloc(lbib_sim *s, double *mass) {
     if (e != cudaSuccess) return cuda_fail(s, e, "mass");
     double dev = 0.0;
     for (int b = 0; b < blocks; ++b) dev += host[b];
-    *mass = (double)s->d.nf * s->p.rho0 + dev;
+    *mass = (double)(s->d.nf - s->d.nsolid) * s->p.rho0 + dev;
     return LBIB_OK;
 }
 
@@ -943,7 +977,8 @@ lbib_status lbib_info(const lbib_sim *s, int64_t out[8]) {
     out[2] = s->nn_total;
     out[3] = s->d.nf;
     out[4] = s->t;
-    out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes + s->rep_bytes);
+    out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes + s->rep_bytes +
+                       (s->solid_mem ? (size_t)s->d.nwords * 4 : 0));
     out[6] = s->p.precision;
     out[7] = 0;
     return LBIB_OK;

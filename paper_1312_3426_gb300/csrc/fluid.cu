@@ -24,18 +24,26 @@
 
 namespace lbib {
 
-template <typename T>
+template <typename T, bool SOLID>
 __global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed) {
-    fluid_block<T>(s, par, blockIdx.x * FLUID_THREADS, seed);
+    fluid_block<T, SOLID>(s, par, blockIdx.x * FLUID_THREADS, seed);
+}
+
+template <typename T>
+static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
+    if (s.solid)
+        k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
+    else
+        k_fluid<T, false><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
 }
 
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st) {
     const uint32_t seed = step_seed(t);
     const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
     switch (s.prec) {
-        case LBIB_POP_F32: k_fluid<float><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
-        case LBIB_POP_F16S: k_fluid<__half><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
-        case LBIB_POP_BF16S: k_fluid<__nv_bfloat16><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed); break;
+        case LBIB_POP_F32: launch_fluid_t<float>(s, par, seed, blocks, st); break;
+        case LBIB_POP_F16S: launch_fluid_t<__half>(s, par, seed, blocks, st); break;
+        case LBIB_POP_BF16S: launch_fluid_t<__nv_bfloat16>(s, par, seed, blocks, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -67,6 +75,17 @@ template <typename T>
 __global__ void k_fields(SimDev s, int pop_par, int gmode, float *u, float *rho_out, int to_ufield) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= s.nf) return;
+    if (s.solid && solid_bit(s, f)) {  // obstacle: no fluid
+        if (to_ufield) {
+            s.ufield[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
+        const int64_t c = full_index(s, f);
+        const int64_t ncell = (int64_t)s.nx * s.ny * s.nz;
+        if (u) u[c] = u[ncell + c] = u[2 * ncell + c] = 0.f;
+        if (rho_out) rho_out[c] = 0.f;
+        return;
+    }
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {

@@ -162,6 +162,7 @@ __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corne
     for (int k = 0; k < 8; ++k) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
         c.f[k] = fluid_index(s, dx ? cx1 : cx0, iy + dy, dz ? cz1 : cz0);
+        if (s.solid && c.f[k] >= 0 && solid_bit(s, c.f[k])) c.f[k] = -1;  // obstacle corner
         c.w[k] = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
     }
 }

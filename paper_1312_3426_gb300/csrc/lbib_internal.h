@@ -151,7 +151,17 @@ struct SimDev {
     int in_on;
     int in_box[6];
     float in_u[3];
+    // obstacle cells (bit per fluid cell, nwords words; null: none): solid
+    // like the wall rows
+    const uint32_t *solid;
+    int nsolid;
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool solid_bit(const SimDev &s, int f) {
+    return (__ldg(s.solid + (f >> 5)) >> (f & 31)) & 1u;
+}
+#endif
 
 // ---- launchers (fluid.cu) -------------------------------------------------
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);

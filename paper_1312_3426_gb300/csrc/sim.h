@@ -59,6 +59,7 @@ struct lbib_sim {
 
     double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects
     double rep_wall[3] = {0, 1, 0};     // and against the walls
+    uint32_t *solid_mem = nullptr;      // obstacle bits (one per fluid cell)
     void *rep_mem = nullptr;            // object boxes, pair list, pair count
     int rep_cap_obj = 0;                // objects the buffers hold
     size_t rep_bytes = 0;

@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
         "lbib_object_set_force": (st, [P, C.c_int, P]),
         "lbib_set_repulsion": (st, [P, P, P]),
         "lbib_set_inlet": (st, [P, P, P]),
+        "lbib_set_solid": (st, [P, P, C.c_int64]),
         "lbib_object_set_nodes": (st, [P, C.c_int, P, C.c_int]),
         "lbib_object_set_velocities": (st, [P, C.c_int, P, C.c_int]),
         "lbib_fluid_init": (st, [P]),
@@ -318,6 +319,15 @@ def lbib_set_repulsion(h, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
     _check(h, _lib.lbib_set_repulsion(h, _p(a), _p(b)))
 
 
+def lbib_set_solid(h, mask):
+    """Obstacle cells from a [nz][ny][nx] boolean mask (None: none)."""
+    if mask is None:
+        _check(h, _lib.lbib_set_solid(h, None, 0))
+        return
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(h, _lib.lbib_set_solid(h, _p(m), int(m.size)))
+
+
 def lbib_set_inlet(h, box, u):
     b = np.ascontiguousarray(box, dtype=np.int32).reshape(6)
     v = _f64(u, (3,))
@@ -443,6 +453,9 @@ class Sim:
         inlet = getattr(scene, "inlet", None)
         if inlet is not None:
             lbib_set_inlet(s.h, *inlet)
+        solid = getattr(scene, "solid", None)
+        if solid is not None:
+            lbib_set_solid(s.h, solid)
         if init:
             s.fluid_init()
         return s

@@ -495,3 +495,46 @@ def test_velocity_inlet_half_storage(prec, bound):
     sc = _inlet_scene(with_objects=False)
     o, g = run_pair(sc, 400, precision=prec, pop_scale_log2=12)
     assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+
+
+# ------------------------------------------------------------- obstacles (Sec. 6 rhomboids)
+
+def _obstacle_scene(with_objects=True, walls=True):
+    from workloads import geometry
+    s = scenes.Scene("posts", 40, 16, 24, walls=walls, body_force=(2e-5, 0.0, 0.0))
+    s.solid = geometry.staggered_rhomboids(40, 16, 24, count=3, seed=5)
+    if with_objects:
+        n2, t2 = mesh.biconcave(2)
+        s.templates.append(scenes.Template(n2, t2, (3.0, 3.0, 3.0), **scenes.PAPER_MODULI))
+        s.objects.append(scenes.Obj(0, (20.0, 8.0, 4.5), (0.3, 0.2, 0.1)))
+        s.objects.append(scenes.Obj(0, (4.0, 8.3, 17.0), (1.2, -0.4, 0.7)))
+    return s
+
+
+def test_obstacles_match_oracle():
+    sc = _obstacle_scene()
+    o, g = run_pair(sc, 300)
+    u = g.velocity()
+    assert np.abs(u[:, sc.solid]).max() == 0.0
+    assert rel_l2(u, o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert abs(g.mass() - o.fluid_totals()[0]) <= 1e-9 * o.fluid_totals()[0]
+
+
+@pytest.mark.parametrize("prec,bound", [("f16s", 1e-3)])
+def test_obstacles_half_storage(prec, bound):
+    sc = _obstacle_scene(with_objects=False, walls=False)
+    o, g = run_pair(sc, 300, precision=prec, pop_scale_log2=12)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+
+
+def test_batch_with_obstacles_equals_alone():
+    scs = [_obstacle_scene(), _two_object_scene(True)]
+    alone = [lbib.Sim.from_scene(s) for s in scs]
+    mixed = [lbib.Sim.from_scene(s) for s in scs]
+    for a in alone:
+        a.step(40)
+    lbib.lbib_batch_step([m.h for m in mixed], 40)
+    for s, a, m in zip(scs, alone, mixed):
+        ua, um = a.velocity(), m.velocity()
+        assert np.abs(ua - um).max() <= 1e-5 * np.abs(ua).max()
