@@ -29,8 +29,22 @@ __global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, u
     fluid_block<T, SOLID>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
+// 16-bit storage, even nx, no obstacles, no inlet: two cells per thread.
+template <typename T>
+__global__ void __launch_bounds__(FLUID_THREADS, 3) k_fluid_pair(SimDev s, int par, uint32_t seed) {
+    const int f = 2 * (int)(blockIdx.x * FLUID_THREADS + threadIdx.x);
+    if (f < s.nf) fluid_pair<T>(s, par, f, seed);
+}
+
 template <typename T>
 static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
+    if constexpr (sizeof(T) == 2) {
+        if ((s.nx & 1) == 0 && !s.solid && !s.in_on) {
+            const int pblocks = (s.nf / 2 + FLUID_THREADS - 1) / FLUID_THREADS;
+            k_fluid_pair<T><<<pblocks, FLUID_THREADS, 0, st>>>(s, par, seed);
+            return;
+        }
+    }
     if (s.solid)
         k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
     else

@@ -338,6 +338,147 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
     if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
 }
 
+// ------------------------------------------------------------------
+// Two cells per thread for 16-bit storage (nx even, no obstacles, no inlet).
+// A thread owns cells f and f+1 (f even, same row).  Populations of the
+// two cells sit next to each other in every plane, so the pair is read as
+// one 32-bit word where the source is even (directions without an x
+// component, bounce-back) and as two 16-bit words at adjacent addresses
+// otherwise, and always written as one 32-bit word; the index, neighbour
+// and address arithmetic and the random bits are shared by the two cells.
+
+template <typename T>
+struct Half2Bits;
+template <>
+struct Half2Bits<__half> {
+    static __device__ __forceinline__ float lo(uint32_t u) { return __half2float(__ushort_as_half((unsigned short)u)); }
+    static __device__ __forceinline__ float hi(uint32_t u) {
+        return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+    }
+    // stochastic rounding of two values (as Raw<__half>::st), 13 random
+    // bits each from the two halves of r
+    static __device__ __forceinline__ uint32_t pack(float a, float b, uint32_t r) {
+        const __half ha = __float2half_rz(__uint_as_float(__float_as_uint(a) + (r & 0x1fffu)));
+        const __half hb = __float2half_rz(__uint_as_float(__float_as_uint(b) + ((r >> 16) & 0x1fffu)));
+        return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+    }
+};
+template <>
+struct Half2Bits<__nv_bfloat16> {
+    static __device__ __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
+    static __device__ __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+    static __device__ __forceinline__ uint32_t pack(float a, float b, uint32_t r) {
+        const uint32_t ba = __float_as_uint(a) + (r & 0xffffu);
+        const uint32_t bb = __float_as_uint(b) + (r >> 16);
+        return (ba >> 16) | (bb & 0xffff0000u);
+    }
+};
+
+// The pair of direction Q arriving at cells f, f+1 (low half: cell f).
+// dxm0: x-1 offset of cell f (wraps at x = 0); dxp1: x+1 offset of cell f+1
+// (wraps at x+1 = nx-1).
+template <int Q>
+__device__ __forceinline__ uint32_t pull2(const uint16_t *__restrict__ src, uint32_t nfp, uint32_t f, const Nbr &n,
+                                          int dxm0, int dxp1) {
+    constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
+    if ((ey == 1 && n.ylo_solid) || (ey == -1 && n.yhi_solid))
+        return __ldg((const unsigned int *)(src + (uint32_t)d3q19_opp(Q) * nfp + f));
+    int g = (int)f;
+    if (ey == 1) g += n.dym;
+    if (ey == -1) g += n.dyp;
+    if (ez == 1) g += n.dzm;
+    if (ez == -1) g += n.dzp;
+    const uint16_t *p = src + (uint32_t)Q * nfp;
+    if (ex == 0) return __ldg((const unsigned int *)(p + (uint32_t)g));  // g even
+    if (ex == 1)  // cell f from x-1, cell f+1 from x
+        return (uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + dxm0))) |
+               ((uint32_t)__ldg((const unsigned short *)(p + (uint32_t)g)) << 16);
+    // ex == -1: cell f from x+1, cell f+1 from x+2 (or the row start)
+    return (uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + 1))) |
+           ((uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + 1 + dxp1))) << 16);
+}
+
+template <typename T>
+__device__ __forceinline__ Moments moments_half(const uint32_t (&P)[NQ], bool high) {
+    float h[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) h[q] = high ? Half2Bits<T>::hi(P[q]) : Half2Bits<T>::lo(P[q]);
+    return moments19(h);
+}
+
+template <typename T, int Q>
+__device__ __forceinline__ void collide2(uint32_t *__restrict__ dst, uint32_t nfp2, uint32_t f2, uint32_t Pq,
+                                         uint32_t Po, const Coll &a, const Coll &b, const CollK &k, float wsc,
+                                         uint32_t &rng) {
+    const float2 ta = pair_terms<Q>(a, k, wsc), tb = pair_terms<Q>(b, k, wsc);
+    rng = rng * 747796405u + 2891336453u;
+    const uint32_t r1 = rng ^ (rng >> 15);
+    rng = rng * 747796405u + 2891336453u;
+    const uint32_t r2 = rng ^ (rng >> 15);
+    __stcs((unsigned int *)(dst + (uint32_t)Q * nfp2 + f2),
+           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(Pq), ta.x), fmaf(k.c1, Half2Bits<T>::hi(Pq), tb.x), r1));
+    __stcs((unsigned int *)(dst + (uint32_t)(Q + 1) * nfp2 + f2),
+           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(Po), ta.y), fmaf(k.c1, Half2Bits<T>::hi(Po), tb.y), r2));
+}
+
+template <typename T>
+__device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uint32_t step_seed) {
+    const uint16_t *__restrict__ src = (const uint16_t *)s.pop[par];
+    uint32_t *__restrict__ dst = (uint32_t *)s.pop[par ^ 1];
+    const uint32_t nfp = (uint32_t)s.nfp, f = (uint32_t)fi;
+    const uint32_t r = s.div_nx.div(f);
+    const uint32_t x = f - r * (uint32_t)s.nx;
+    const uint32_t z = s.div_nyf.div(r);
+    const uint32_t y = r - z * (uint32_t)s.nyf;
+    const Nbr n = neighbours(s, (int)x, (int)y, (int)z);
+    const int dxm0 = n.dxm, dxp1 = ((int)x + 2 == s.nx) ? -(s.nx - 1) : 1;
+
+    uint32_t P[NQ];
+#define LBIB_PULL2(q) P[q] = pull2<q>(src, nfp, f, n, dxm0, dxp1);
+    LBIB_PULL2(0) LBIB_PULL2(1) LBIB_PULL2(2) LBIB_PULL2(3) LBIB_PULL2(4) LBIB_PULL2(5) LBIB_PULL2(6)
+    LBIB_PULL2(7) LBIB_PULL2(8) LBIB_PULL2(9) LBIB_PULL2(10) LBIB_PULL2(11) LBIB_PULL2(12) LBIB_PULL2(13)
+    LBIB_PULL2(14) LBIB_PULL2(15) LBIB_PULL2(16) LBIB_PULL2(17) LBIB_PULL2(18)
+#undef LBIB_PULL2
+
+    const uint32_t act = (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u;
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+    if (act & 1u) {  // spread force of this step; clear the buffer of the next
+        ga = __ldcg(s.G[par] + f);
+        s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (act & 2u) {
+        gb = __ldcg(s.G[par] + f + 1);
+        s.G[par ^ 1][f + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const CollK k = make_collk(s);
+    float rhoa, rhob, usqa, usqb;
+    const Moments ma = moments_half<T>(P, false);
+    const Coll a = make_coll(s, k, ma.r, ma.x, ma.y, ma.z, s.gx + ga.x, s.gy + ga.y, s.gz + ga.z, rhoa, usqa);
+    const Moments mb = moments_half<T>(P, true);
+    const Coll b = make_coll(s, k, mb.r, mb.x, mb.y, mb.z, s.gx + gb.x, s.gy + gb.y, s.gz + gb.z, rhob, usqb);
+    const float sc = s.scale;
+    const float wsc0 = (float)d3q19_w(0) * sc, wsc1 = (float)d3q19_w(1) * sc, wsc2 = (float)d3q19_w(7) * sc;
+    const uint32_t nfp2 = nfp / 2, f2 = f / 2;
+    uint32_t rng = mix32(f ^ step_seed);
+    rng = rng * 747796405u + 2891336453u;
+    __stcs((unsigned int *)(dst + f2),
+           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(P[0]), wsc0 * fmaf(k.om, a.K, -k.fp * a.uG3)),
+                              fmaf(k.c1, Half2Bits<T>::hi(P[0]), wsc0 * fmaf(k.om, b.K, -k.fp * b.uG3)),
+                              rng ^ (rng >> 15)));
+    collide2<T, 1>(dst, nfp2, f2, P[1], P[2], a, b, k, wsc1, rng);
+    collide2<T, 3>(dst, nfp2, f2, P[3], P[4], a, b, k, wsc1, rng);
+    collide2<T, 5>(dst, nfp2, f2, P[5], P[6], a, b, k, wsc1, rng);
+    collide2<T, 7>(dst, nfp2, f2, P[7], P[8], a, b, k, wsc2, rng);
+    collide2<T, 9>(dst, nfp2, f2, P[9], P[10], a, b, k, wsc2, rng);
+    collide2<T, 11>(dst, nfp2, f2, P[11], P[12], a, b, k, wsc2, rng);
+    collide2<T, 13>(dst, nfp2, f2, P[13], P[14], a, b, k, wsc2, rng);
+    collide2<T, 15>(dst, nfp2, f2, P[15], P[16], a, b, k, wsc2, rng);
+    collide2<T, 17>(dst, nfp2, f2, P[17], P[18], a, b, k, wsc2, rng);
+    if (act & 1u) s.ufield[f] = make_float4(a.ux, a.uy, a.uz, rhoa);
+    if (act & 2u) s.ufield[f + 1] = make_float4(b.ux, b.uy, b.uz, rhob);
+    if (!(usqa < 0.09f) || !(usqb < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
+}
+
 // Seed of the rounding bits of step t.
 __host__ __device__ __forceinline__ uint32_t step_seed(long long t) {
     uint32_t x = (uint32_t)t * 0x9e3779b9u + 0x632be5abu;

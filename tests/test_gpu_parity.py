@@ -334,6 +334,19 @@ def test_shifted_half_storage_poiseuille_error(prec, bound):
     assert rel_l2(g32.velocity(), o32.velocity(), sc) < err
 
 
+@pytest.mark.parametrize("prec,bound", [("f16s", 5e-3), ("bf16s", 5e-2)])
+@pytest.mark.parametrize("walls", [True, False])
+def test_half_storage_two_cells_per_thread(prec, bound, walls):
+    """Even nx selects the two-cells-per-thread kernel for 16-bit storage;
+    nx = 38 puts row starts inside warps, the x wrap inside pairs' reach and
+    a ragged last block; two objects make active cells."""
+    sc = _two_object_scene(walls, nx=38, ny=19, nz=29)
+    assert sc.nx % 2 == 0 and (sc.n_fluid_cells // 2) % 256 != 0
+    o, g = run_pair(sc, 300, precision=prec, pop_scale_log2=12)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+    assert nodes_maxabs(g, o, 2) <= 1e-3
+
+
 # ------------------------------------------------------------- batching
 
 def test_batch_step_equals_individual_steps():
