@@ -37,16 +37,28 @@ constexpr int LBIB_BATCH_GRAPH_STEPS = 16;  // steps per captured graph
 
 extern __shared__ float batch_smem[];
 
-// One launch per storage type and obstacle flag present in the batch (items
-// grouped by both).
-template <typename T, bool SOLID>
+// One launch per storage type and boundary-condition variant present in the
+// batch (items grouped by both; BC: obstacles or an inlet).
+template <typename T, bool BC>
 __global__ void __launch_bounds__(FLUID_THREADS, 5)
     k_batch_fluid(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
                   const int2 *__restrict__ items) {
     const int2 it = items[blockIdx.x];  // (simulation, block of cells)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
-    fluid_block<T, SOLID>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
+    fluid_block<T, BC>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
+}
+
+// 16-bit storage, even nx, plain boundaries: two cells per thread.
+template <typename T>
+__global__ void __launch_bounds__(FLUID_THREADS, 3)
+    k_batch_fluid_pair(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
+                       const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];  // (simulation, block of FLUID_THREADS cell pairs)
+    const SimDev &s = sims[it.x];
+    const long long t = t_base[it.x] + step_off;
+    const int f = 2 * (it.y * FLUID_THREADS + (int)threadIdx.x);
+    if (f < s.nf) fluid_pair<T>(s, (int)(t & 1), f, step_seed(t));
 }
 
 __global__ void __launch_bounds__(IB_THREADS, 3)
@@ -76,13 +88,13 @@ __global__ void k_batch_advance(long long *t_base, int n, int steps) {
 struct BatchPlan {
     std::vector<lbib_sim *> sims;
     std::vector<uint64_t> serial;  // identity of each simulation (addresses can be reused)
-    std::vector<int> nobj, nn;
+    std::vector<int> nobj, nn, group;  // group: fluid kernel variant (2 * precision + BC)
     std::vector<SimDev> dev;  // descriptors the device copy holds
     int cluster = 0, device = -1;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
     int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
-    int n_flp[6] = {0, 0, 0, 0, 0, 0};  // fluid items per group 2 * precision + has-obstacles
+    int n_flp[8] = {};  // fluid items per kernel variant (see fluid_group)
     int n_fl = 0, n_nd = 0, n_mb = 0;
     int max_nodes = 0;
     cudaStream_t aux = nullptr;   // membrane kernel
@@ -106,17 +118,27 @@ struct BatchPlan {
         serial.clear();
         nobj.clear();
         nn.clear();
+        group.clear();
         dev.clear();
     }
 };
 
 static BatchPlan g_plan;
 
+// Fluid kernel variant of a simulation: 2 * precision + BC (obstacles or an
+// inlet) for the one-cell-per-thread kernels; 6 / 7 for the two-cells
+// kernels of FP16 / BF16 storage (even nx, plain boundaries).
+static int fluid_group(const lbib_sim *s) {
+    const bool bc = s->d.solid || s->d.in_on;
+    if (s->d.prec != LBIB_POP_F32 && (s->d.nx & 1) == 0 && !bc) return 6 + (s->d.prec - 1);
+    return 2 * s->d.prec + (bc ? 1 : 0);
+}
+
 static bool plan_matches(lbib_sim *const *sims, int n, int cluster) {
     if ((int)g_plan.sims.size() != n || g_plan.cluster != cluster || g_plan.device != sims[0]->device) return false;
     for (int i = 0; i < n; ++i)
         if (g_plan.sims[i] != sims[i] || g_plan.serial[i] != sims[i]->serial ||
-            g_plan.nobj[i] != (int)sims[i]->objs.size() ||
+            g_plan.nobj[i] != (int)sims[i]->objs.size() || g_plan.group[i] != fluid_group(sims[i]) ||
             g_plan.nn[i] != sims[i]->nn_total)
             return false;
     return true;
@@ -143,19 +165,21 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_membrane, cudaEventDisableTiming);
         if (e != cudaSuccess) return e;
     }
-    std::vector<int2> flp[6], fl, nd, mb;
+    std::vector<int2> flp[8], fl, nd, mb;
     int max_nodes = 0;
     for (int i = 0; i < n; ++i) {
         const lbib_sim *s = sims[i];
-        const int blocks = (s->d.nf + FLUID_THREADS - 1) / FLUID_THREADS;
-        for (int b = 0; b < blocks; ++b) flp[2 * s->d.prec + (s->d.solid ? 1 : 0)].push_back(make_int2(i, b));
+        const int grp = fluid_group(s);
+        const int cells_per_block = grp >= 6 ? 2 * FLUID_THREADS : FLUID_THREADS;
+        const int blocks = (s->d.nf + cells_per_block - 1) / cells_per_block;
+        for (int b = 0; b < blocks; ++b) flp[grp].push_back(make_int2(i, b));
         if (!s->objs.empty()) {
             for (int f = 0; f < s->nn_total; f += IB_THREADS) nd.push_back(make_int2(i, f));
             for (int o = 0; o < (int)s->objs.size(); ++o) mb.push_back(make_int2(i, o));
             max_nodes = std::max(max_nodes, s->max_nodes);
         }
     }
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 8; ++k) {
         g_plan.n_flp[k] = (int)flp[k].size();
         fl.insert(fl.end(), flp[k].begin(), flp[k].end());
     }
@@ -174,6 +198,7 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
     g_plan.sims.assign(sims, sims + n);
     for (int i = 0; i < n; ++i) {
         g_plan.serial.push_back(sims[i]->serial);
+        g_plan.group.push_back(fluid_group(sims[i]));
         g_plan.nobj.push_back((int)sims[i]->objs.size());
         g_plan.nn.push_back(sims[i]->nn_total);
     }
@@ -247,6 +272,10 @@ static cudaError_t enqueue_steps(cudaStream_t st, int step_off, int k) {
             if (n[4]) k_batch_fluid<__nv_bfloat16, false><<<n[4], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
             g += n[4];
             if (n[5]) k_batch_fluid<__nv_bfloat16, true><<<n[5], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[5];
+            if (n[6]) k_batch_fluid_pair<__half><<<n[6], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            g += n[6];
+            if (n[7]) k_batch_fluid_pair<__nv_bfloat16><<<n[7], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (g_plan.n_nd) e = cudaStreamWaitEvent(st, g_plan.ev_membrane, 0);

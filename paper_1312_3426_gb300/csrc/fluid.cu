@@ -24,9 +24,9 @@
 
 namespace lbib {
 
-template <typename T, bool SOLID>
+template <typename T, bool BC>
 __global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed) {
-    fluid_block<T, SOLID>(s, par, blockIdx.x * FLUID_THREADS, seed);
+    fluid_block<T, BC>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
 // 16-bit storage, even nx, no obstacles, no inlet: two cells per thread.
@@ -45,7 +45,7 @@ static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, 
             return;
         }
     }
-    if (s.solid)
+    if (s.solid || s.in_on)
         k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
     else
         k_fluid<T, false><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);

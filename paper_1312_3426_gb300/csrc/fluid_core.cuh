@@ -106,10 +106,10 @@ struct Raw<__nv_bfloat16> {
     }
 };
 
-// Pull the (raw) population of direction Q arriving at cell f.  With
-// obstacles (SOLID), a population coming from an obstacle cell is the
-// cell's own opposite one, as at the walls.
-template <typename T, int Q, bool SOLID>
+// Pull the (raw) population of direction Q arriving at cell f.  In the
+// boundary-condition variant (BC) a population coming from an obstacle cell
+// is the cell's own opposite one, as at the walls.
+template <typename T, int Q, bool BC>
 __device__ __forceinline__ float pull(const SimDev &s, const T *__restrict__ src, uint32_t nfp, uint32_t f,
                                       const Nbr &n) {
     constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
@@ -122,7 +122,7 @@ __device__ __forceinline__ float pull(const SimDev &s, const T *__restrict__ src
     if (ey == -1) g += n.dyp;
     if (ez == 1) g += n.dzm;
     if (ez == -1) g += n.dzp;
-    if (SOLID && Q != 0 && solid_bit(s, g)) return Raw<T>::ld(src + (uint32_t)d3q19_opp(Q) * nfp + f);
+    if (BC && Q != 0 && s.solid && solid_bit(s, g)) return Raw<T>::ld(src + (uint32_t)d3q19_opp(Q) * nfp + f);
     return Raw<T>::ld(src + (uint32_t)Q * nfp + (uint32_t)g);
 }
 
@@ -276,13 +276,15 @@ __device__ __forceinline__ void inlet_cell(const SimDev &s, int x, int yl, int z
     h[18] = inlet_eq<18>(drho, rho, usq, u, sc);
 }
 
-template <typename T, bool SOLID>
+// BC: the variant for simulations with obstacles or a velocity inlet (the
+// plain variant carries no test for either).
+template <typename T, bool BC>
 __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, bool active, uint32_t step_seed) {
     static_assert(d3q19_opp(1) == 2 && d3q19_opp(17) == 18, "directions 2k-1, 2k must be opposite");
     const T *__restrict__ src = (const T *)s.pop[par];
     T *__restrict__ dst = (T *)s.pop[par ^ 1];
     const uint32_t nfp = (uint32_t)s.nfp, f = (uint32_t)fi;
-    if (SOLID && solid_bit(s, fi)) return;  // an obstacle cell holds no fluid
+    if (BC && s.solid && solid_bit(s, fi)) return;  // an obstacle cell holds no fluid
     const uint32_t r = s.div_nx.div(f);
     const uint32_t x = f - r * (uint32_t)s.nx;
     const uint32_t z = s.div_nyf.div(r);
@@ -290,13 +292,13 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
     const Nbr n = neighbours(s, (int)x, (int)y, (int)z);
 
     float h[NQ];
-#define LBIB_PULL(q) h[q] = pull<T, q, SOLID>(s, src, nfp, f, n);
+#define LBIB_PULL(q) h[q] = pull<T, q, BC>(s, src, nfp, f, n);
     LBIB_PULL(0) LBIB_PULL(1) LBIB_PULL(2) LBIB_PULL(3) LBIB_PULL(4) LBIB_PULL(5) LBIB_PULL(6)
     LBIB_PULL(7) LBIB_PULL(8) LBIB_PULL(9) LBIB_PULL(10) LBIB_PULL(11) LBIB_PULL(12) LBIB_PULL(13)
     LBIB_PULL(14) LBIB_PULL(15) LBIB_PULL(16) LBIB_PULL(17) LBIB_PULL(18)
 #undef LBIB_PULL
 
-    if (s.in_on) inlet_cell(s, (int)x, (int)y + s.walls, (int)z, h);
+    if (BC && s.in_on) inlet_cell(s, (int)x, (int)y + s.walls, (int)z, h);
 
     float Gx = s.gx, Gy = s.gy, Gz = s.gz;
     if (active) {  // spread force of this step; clear the buffer of the next
@@ -497,11 +499,11 @@ __device__ __forceinline__ uint32_t active_word(const SimDev &s, int f) {
 }
 
 // One block of FLUID_THREADS consecutive fluid cells starting at f0.
-template <typename T, bool SOLID>
+template <typename T, bool BC>
 __device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0, uint32_t step_seed) {
     const int f = f0 + (int)threadIdx.x;
     const uint32_t act = active_word(s, f);
-    if (f < s.nf) fluid_cell<T, SOLID>(s, par, f, (act >> (threadIdx.x & 31)) & 1u, step_seed);
+    if (f < s.nf) fluid_cell<T, BC>(s, par, f, (act >> (threadIdx.x & 31)) & 1u, step_seed);
 }
 
 }  // namespace lbib
