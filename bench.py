@@ -263,8 +263,9 @@ def batch_workload(args, lbib, torch, dev, stream):
     nodes = sum(sc.n_nodes for sc in scs)
     for s in sims:
         s.close()
-    return scs, cells, nodes, ms, clocks, {"ib_cluster": choice[0], "overlap": choice[1],
-                                           "candidates_s": {f"{k[0]}/{k[1]}": round(v, 5) for k, v in timing.items()}}
+    return scs, cells, nodes, ms, clocks, {"ib_cluster": choice[0], "overlap": choice[1], "membrane_threads": choice[2],
+                                           "candidates_s": {"/".join(map(str, k)): round(v, 5)
+                                                            for k, v in timing.items()}}
 
 
 def serving_comparison(args, stream):

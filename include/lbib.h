@@ -340,10 +340,18 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * stream at the start of each step.  LBIB_TUNE_MEMBRANE_CLUSTERS: number of
  * clusters of the membrane-force kernel, each looping over the objects
  * (0, default: one cluster per object; a small grid leaves most SMs to the
- * fluid kernel running beside it).  Results do not depend on the knobs
- * beyond the order of floating-point atomics.  LBIB_ERR_ARG for an unknown
- * key or an out-of-range value. */
-typedef enum { LBIB_TUNE_IB_CLUSTER = 0, LBIB_TUNE_OVERLAP = 1, LBIB_TUNE_MEMBRANE_CLUSTERS = 2 } lbib_tune_key;
+ * fluid kernel running beside it).  LBIB_TUNE_MEMBRANE_THREADS: threads per
+ * block of the membrane-force kernel (a multiple of 32 in [32, 256],
+ * default 192: fewer threads leave more of each SM to the fluid kernel
+ * running beside it).  Results do not depend on the knobs beyond the order
+ * of floating-point atomics.  LBIB_ERR_ARG for an unknown key or an
+ * out-of-range value. */
+typedef enum {
+    LBIB_TUNE_IB_CLUSTER = 0,
+    LBIB_TUNE_OVERLAP = 1,
+    LBIB_TUNE_MEMBRANE_CLUSTERS = 2,
+    LBIB_TUNE_MEMBRANE_THREADS = 3
+} lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);
 

@@ -90,7 +90,7 @@ struct BatchPlan {
     std::vector<uint64_t> serial;  // identity of each simulation (addresses can be reused)
     std::vector<int> nobj, nn, group;  // group: fluid kernel variant (2 * precision + BC)
     std::vector<SimDev> dev;  // descriptors the device copy holds
-    int cluster = 0, device = -1;
+    int cluster = 0, device = -1, mthreads = IB_THREADS;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
     int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
@@ -224,7 +224,7 @@ static cudaError_t launch_membrane_batch(cudaStream_t st) {
     if (g_plan.n_mb == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(g_plan.n_mb * g_plan.cluster));
-    cfg.blockDim = dim3(IB_THREADS);
+    cfg.blockDim = dim3((unsigned)g_plan.mthreads);
     cfg.dynamicSmemBytes = ib_smem_bytes(g_plan.max_nodes);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -331,6 +331,10 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     cudaError_t e = cudaSuccess;
     const int cluster = sims[0]->cluster;
     if (!plan_matches(sims, n, cluster)) e = build_plan(sims, n, cluster, st);
+    if (g_plan.mthreads != sims[0]->membrane_threads) {
+        g_plan.mthreads = sims[0]->membrane_threads;  // captured in the graph
+        g_plan.release_graph();
+    }
     // descriptors (node arrays may have been reallocated, tables uploaded)
     // and the step counters of this call
     std::vector<long long> tb(n);

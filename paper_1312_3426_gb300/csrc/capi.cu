@@ -707,7 +707,7 @@ static lbib_status launch_membrane_timed(lbib_sim *s, cudaStream_t st) {
         if (r != LBIB_OK) return r;
         LBIB_CUDA(s, cudaEventRecord(ev[0], st), "profile event");
     }
-    LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, st), "membrane forces");
+    LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, s->membrane_threads, st), "membrane forces");
     LBIB_CUDA(s, launch_repulsion(s->d, s->max_nodes, st), "repulsion");
     if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], st), "profile event");
     return LBIB_OK;
@@ -1026,6 +1026,11 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         s->overlap = value != 0;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_MEMBRANE_THREADS) {
+        if (value < 32 || value > IB_THREADS || value % 32) return fail(s, LBIB_ERR_ARG, "membrane threads must be a multiple of 32 in [32, 256]");
+        s->membrane_threads = value;
+        return LBIB_OK;
+    }
     if (key == LBIB_TUNE_MEMBRANE_CLUSTERS) {
         if (value < 0 || value > (1 << 20)) return fail(s, LBIB_ERR_ARG, "membrane clusters must be in [0, 2^20]");
         s->membrane_clusters = value;
@@ -1042,6 +1047,10 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
     }
     if (key == LBIB_TUNE_OVERLAP) {
         *value = s->overlap ? 1 : 0;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_MEMBRANE_THREADS) {
+        *value = s->membrane_threads;
         return LBIB_OK;
     }
     if (key == LBIB_TUNE_MEMBRANE_CLUSTERS) {

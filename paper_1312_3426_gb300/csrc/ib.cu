@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(IB_THREADS, 4) k_nodes(SimDev s, int par) {
     if (i < s.nn_total) node_step(s, i, par);
 }
 
-cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, cudaStream_t st) {
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads,
+                            cudaStream_t st) {
     if (s.nobj == 0) return cudaSuccess;
     const size_t smem = ib_smem_bytes(max_nodes);
     static size_t configured = 0;
@@ -35,7 +36,7 @@ cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max
     cudaLaunchConfig_t cfg = {};
     const int n_clusters = (max_clusters > 0 && max_clusters < s.nobj) ? max_clusters : s.nobj;
     cfg.gridDim = dim3((unsigned)(n_clusters * cluster));
-    cfg.blockDim = dim3(IB_THREADS);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];

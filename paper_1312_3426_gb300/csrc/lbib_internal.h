@@ -183,7 +183,9 @@ cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int
 // membrane part: clusters of `cluster` blocks, one per object or at most
 // max_clusters (> 0) looping over the objects (max_nodes sizes shared
 // memory); coupling part: one thread per node
-cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, cudaStream_t st);
+// threads: block size (a multiple of 32, at most IB_THREADS)
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads,
+                            cudaStream_t st);
 cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st);
 // object-object repulsion added to Fel (after the membrane kernel, which
 // also writes the object bounding boxes); max_nodes sizes shared memory

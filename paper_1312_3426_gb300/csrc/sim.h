@@ -56,6 +56,7 @@ struct lbib_sim {
     bool fel_valid = false;             // Fel holds the membrane forces of the current node positions
     bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
+    int membrane_threads = 192;         // block size of the membrane kernel
 
     double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects
     double rep_wall[3] = {0, 1, 0};     // and against the walls

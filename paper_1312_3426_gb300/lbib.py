@@ -290,6 +290,7 @@ def lbib_objects_analyze(h, n_obj, out=None):
 LBIB_TUNE_IB_CLUSTER = 0
 LBIB_TUNE_OVERLAP = 1
 LBIB_TUNE_MEMBRANE_CLUSTERS = 2
+LBIB_TUNE_MEMBRANE_THREADS = 3
 
 
 def lbib_set_tuning(h, key, value):

@@ -2,8 +2,9 @@
 
 The knobs (``lbib_set_tuning``) change no result beyond the order of
 floating-point atomics, only the speed: the thread blocks per object of the
-membrane-force kernel (``LBIB_TUNE_IB_CLUSTER``) and whether that kernel
-overlaps the fluid kernel on a second stream (``LBIB_TUNE_OVERLAP``).
+membrane-force kernel (``LBIB_TUNE_IB_CLUSTER``), its block size
+(``LBIB_TUNE_MEMBRANE_THREADS``) and whether that kernel overlaps the fluid
+kernel on a second stream (``LBIB_TUNE_OVERLAP``).
 ``autotune`` times a few steps of the caller's own simulations for each
 candidate and keeps the fastest; results are cached by a key of the
 workload's shape (box-size class, storage precision, largest template), so
@@ -47,9 +48,10 @@ def _time(sims, steps, batched):
     return time.perf_counter() - t0
 
 
-def autotune(sims, clusters=(1, 2, 4), overlaps=(1, 0), steps=32, batched=None):
-    """Chooses and applies the fastest (cluster, overlap) for `sims` (Sim
-    objects); returns the choice and the measured seconds per candidate."""
+def autotune(sims, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), steps=32, batched=None):
+    """Chooses and applies the fastest (cluster, overlap, membrane threads)
+    for `sims` (Sim objects); returns the choice and the measured seconds
+    per candidate."""
     sims = list(sims)
     if batched is None:
         batched = len(sims) > 1
@@ -59,20 +61,22 @@ def autotune(sims, clusters=(1, 2, 4), overlaps=(1, 0), steps=32, batched=None):
         _apply(sims, *best)
         return _CACHE[key]
     if not any(s.obj_tid for s in sims):
-        best, timing = (1, 1), {}
+        best, timing = (1, 1, 192), {}
     else:
         timing = {}
         for c in clusters:
             for ov in overlaps:
-                _apply(sims, c, ov)
-                timing[(c, ov)] = _time(sims, steps, batched)
+                for th in threads:
+                    _apply(sims, c, ov, th)
+                    timing[(c, ov, th)] = _time(sims, steps, batched)
         best = min(timing, key=timing.get)
     _apply(sims, *best)
     _CACHE[key] = (best, timing)
     return _CACHE[key]
 
 
-def _apply(sims, cluster, overlap):
+def _apply(sims, cluster, overlap, threads=192):
     for s in sims:
         lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_IB_CLUSTER, cluster)
         lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_OVERLAP, overlap)
+        lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, threads)

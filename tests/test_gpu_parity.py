@@ -177,8 +177,9 @@ def test_objects_crossing_the_periodic_boundary():
     assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
 
 
-@pytest.mark.parametrize("overlap,cluster,mclusters,chunk", [(1, 2, 0, 40), (1, 3, 1, 1), (0, 1, 0, 7), (0, 8, 1, 40)])
-def test_launch_knobs_chunks_and_midrun_node_change(overlap, cluster, mclusters, chunk):
+@pytest.mark.parametrize("overlap,cluster,mclusters,threads,chunk",
+                         [(1, 2, 0, 256, 40), (1, 3, 1, 64, 1), (0, 1, 0, 192, 7), (0, 8, 1, 128, 40)])
+def test_launch_knobs_chunks_and_midrun_node_change(overlap, cluster, mclusters, threads, chunk):
     """The membrane forces of the next step are computed ahead of time (on a
     second stream when overlap is on); replacing nodes between calls must
     discard them.  Knobs and call granularity change no result beyond the
@@ -189,6 +190,7 @@ def test_launch_knobs_chunks_and_midrun_node_change(overlap, cluster, mclusters,
     lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_OVERLAP, overlap)
     lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_IB_CLUSTER, cluster)
     lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, mclusters)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, threads)
     assert lbib.lbib_get_tuning(g.h, lbib.LBIB_TUNE_OVERLAP) == overlap
 
     def advance(n):
