@@ -283,6 +283,12 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     const int NN = s.nn_total;
     float *Xh = s.Xh, *Xl = s.Xl, *Vh = s.Vh, *Vl = s.Vl;
     df x{Xh[i], Xl[i]}, y{Xh[NN + i], Xl[NN + i]}, z{Xh[2 * NN + i], Xl[2 * NN + i]};
+    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) {
+        // a failed simulation (already flagged): no coupling, so that its
+        // nodes do not pile reductions onto one cell
+        atomicOr(s.status, ST_NODE_NAN);
+        return;
+    }
     df vx{Vh[i], Vl[i]}, vy{Vh[NN + i], Vl[NN + i]}, vz{Vh[2 * NN + i], Vl[2 * NN + i]};
     Corners c;
     corners(s, x, y, z, c);

@@ -187,9 +187,18 @@ def _log_uniform_int(rng, lo, hi):
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
 
 
+def _min_radius(level: int) -> float:
+    """Smallest radius at which a level-`level` mesh keeps its mean edge at
+    0.5 lu or more (edge ~ 1.05 R / 2^level): finer meshes make the explicit
+    membrane update unstable at the paper's moduli with unit node mass."""
+    return 0.5 * 2 ** level / 1.05
+
+
 def batch_mix(n_sims: int = 64, seed: int = 3, steps: int = 100) -> list:
     """Independent channels: box log-uniform per axis in [32, (128,64,64)],
-    0-40 biconcave cells of level 2, 3 or 4, radius scaled to the box."""
+    0-40 biconcave cells of level 2, 3 or 4, radius scaled to the box (at
+    least the level's stable minimum; a level that does not fit the box at
+    that radius drops to the next lower one)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_sims):
@@ -199,6 +208,9 @@ def batch_mix(n_sims: int = 64, seed: int = 3, steps: int = 100) -> list:
         count = int(rng.integers(0, 41))
         level = int(rng.choice([2, 3, 4]))
         radius = float(min(8.0, max(3.0, 0.2 * min(nx, ny - 2, nz))))
+        while level > 2 and 2.0 * max(radius, _min_radius(level)) + 4.0 > min(nx, ny - 2, nz):
+            level -= 1
+        radius = max(radius, _min_radius(level))
         s = Scene(f"batch{i}_{nx}x{ny}x{nz}", nx, ny, nz, steps=steps)
         nodes, tris = _mesh.biconcave(level)
         s.templates.append(Template(nodes, tris, (radius,) * 3, **PAPER_MODULI))
