@@ -70,6 +70,7 @@ def _load():
         "oracle_set_repulsion": (C.c_int, [P, dp, dp]),
         "oracle_set_inlet": (C.c_int, [P, ip, dp]),
         "oracle_set_solid": (C.c_int, [P, P]),
+        "oracle_template_set_kal_direction": (C.c_int, [P, C.c_int, C.c_int]),
         "oracle_repulsion_forces": (None, [P, dp]),
         "oracle_read_velocity": (None, [P, dp]),
         "oracle_set_velocity": (None, [P, dp]),
@@ -219,6 +220,10 @@ class Oracle:
         """Velocity inlet over cells box = (x0, x1, y0, y1, z0, z1) (half-open)."""
         self._lib.oracle_set_inlet(self._h, np.ascontiguousarray(box, dtype=np.int32),
                                    np.ascontiguousarray(u, dtype=np.float64))
+
+    def template_set_kal_direction(self, tid, altitude):
+        if self._lib.oracle_template_set_kal_direction(self._h, tid, int(bool(altitude))) != 0:
+            raise ValueError("unknown template")
 
     def set_solid(self, mask):
         """Obstacle cells from a [nz][ny][nx] boolean mask (None: none)."""

@@ -60,6 +60,7 @@ typedef struct {
     double Sg0, V0;
     double ks, kb, kal, kag, kv;
     int nonlinear;
+    int kal_altitude;     /* local area along the altitudes instead of centroid -> vertex */
 } otpl;
 
 typedef struct {
@@ -517,10 +518,35 @@ static void membrane_forces(const otpl *T, const double *X, double *F, int mask)
                 double w[3];
                 sub3(P, cen, w);
                 double wl = norm3(w);
+                double h[3], hl = 1.0;
+                if (T->kal_altitude) {
+                    /* the second direction of Sec. 4: along the altitude
+                     * through the vertex, from the foot on the opposite
+                     * edge to the vertex */
+                    const double *Q = X + 3 * v[(j + 1) % 3], *R = X + 3 * v[(j + 2) % 3];
+                    double e[3], d[3];
+                    sub3(R, Q, e);
+                    sub3(P, Q, d);
+                    const double s = dot3(d, e) / dot3(e, e);
+                    for (int k = 0; k < 3; ++k) h[k] = d[k] - s * e[k];
+                    hl = norm3(h);
+                } else {
+                    for (int k = 0; k < 3; ++k) h[k] = w[k];
+                    hl = wl;
+                }
                 for (int k = 0; k < 3; ++k)
-                    F[3 * v[j] + k] += (cl + cg) * w[k] / wl + cv * nin[k];
+                    F[3 * v[j] + k] += cl * h[k] / hl + cg * w[k] / wl + cv * nin[k];
             }
         }
+}
+
+/* Direction of the local-area force of template tid (Sec. 4 names two:
+ * 0 = from the centroid to the vertex, 1 = along the vertex's altitude). */
+int oracle_template_set_kal_direction(osim *s, int tid, int altitude)
+{
+    if (tid < 0 || tid >= s->ntpl) return -2;
+    s->tpl[tid].kal_altitude = altitude ? 1 : 0;
+    return 0;
 }
 
 /* Elastic forces of one object at its current nodes (cleared first). */

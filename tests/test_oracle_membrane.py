@@ -346,3 +346,51 @@ def test_rotation_order_and_translation():
     step1 = np.stack([nodes[:, 0], -nodes[:, 2], nodes[:, 1]], 1)
     exp2 = np.stack([step1[:, 2], step1[:, 1], -step1[:, 0]], 1)
     assert np.abs(X2 - exp2).max() < 1e-15
+
+
+def test_local_area_along_altitudes_is_the_normalised_area_gradient():
+    """Second direction of Sec. 4 for the local-area force: along each
+    vertex's altitude.  That direction is the direction of the gradient of
+    the triangle's area with respect to the vertex, taken here by central
+    finite differences of the area, an independent route."""
+    nodes, tris = mesh.icosphere(0)
+    o = oracle.Oracle(20, 20, 20, walls=False)
+    o.template_create(nodes, tris, (3.0, 2.0, 1.5), kal=0.1)   # stretched: non-equilateral triangles
+    o.template_set_kal_direction(0, True)
+    o.object_add(0, (10.0, 10.0, 10.0))
+    X0, _ = o.read_nodes(0)
+    rng = np.random.default_rng(3)
+    X = X0 + rng.normal(0.0, 0.05, X0.shape)
+    o.object_set_nodes(0, X)
+    F = o.membrane_forces(0, 4)
+    area = lambda a, b, c: 0.5 * np.linalg.norm(np.cross(b - a, c - a))  # noqa: E731
+    S0 = [area(*X0[t]) for t in tris]
+    exp = np.zeros_like(X)
+    h = 1e-6
+    for t, s0 in zip(tris, S0):
+        P = X[t].copy()
+        S = area(*P)
+        for j in range(3):
+            g = np.zeros(3)
+            for k in range(3):
+                Pp, Pm = P.copy(), P.copy()
+                Pp[j, k] += h
+                Pm[j, k] -= h
+                g[k] = (area(*Pp) - area(*Pm)) / (2 * h)
+            exp[t[j]] += -0.1 * (S - s0) / S * g / np.linalg.norm(g)
+    assert np.abs(F - exp).max() < 1e-8 * np.abs(exp).max()
+
+
+def test_local_area_directions_agree_on_equilateral_faces():
+    nodes, tris = mesh.icosphere(0)   # regular icosahedron: every face equilateral
+    out = []
+    for alt in (False, True):
+        o = oracle.Oracle(20, 20, 20, walls=False)
+        o.template_create(nodes, tris, (2.0, 2.0, 2.0), kal=0.1)
+        o.template_set_kal_direction(0, alt)
+        o.object_add(0, (10.0, 10.0, 10.0))
+        X0, _ = o.read_nodes(0)
+        o.object_set_nodes(0, 10.0 + (X0 - 10.0) * 1.1)   # uniform inflation keeps faces equilateral
+        out.append(o.membrane_forces(0, 4))
+    assert np.abs(out[1]).max() > 0
+    assert np.allclose(out[0], out[1], rtol=1e-12, atol=1e-15)
