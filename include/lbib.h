@@ -160,6 +160,13 @@ LBIB_API lbib_status lbib_object_add(lbib_sim *sim, int oid, int tid, const doub
  * At most 32 close object pairs per object (sticky LBIB_ERR_NOMEM beyond). */
 LBIB_API lbib_status lbib_set_repulsion(lbib_sim *sim, const double object[3], const double wall[3]);
 
+/* Direction of the local-area force of template tid (Sec. 4 discusses two):
+ * altitude = 0 (default) from the triangle's centroid to the vertex, 1
+ * along the vertex's altitude (from the foot on the opposite edge to the
+ * vertex).  The global-area force keeps the centroid direction.
+ * LBIB_ERR_ID for an unknown template. */
+LBIB_API lbib_status lbib_template_set_kal_direction(lbib_sim *sim, int tid, int altitude);
+
 /* Obstacle cells (the rhomboid obstacles of the Sec. 6 channel): mask
  * [nz][ny][nx] bytes, non-zero = solid; n must be nx*ny*nz.  Entries in the
  * wall rows are ignored.  Obstacle cells hold no fluid and are treated like

@@ -468,6 +468,7 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     dv.kag = (float)kag;
     dv.kv = (float)kv;
     dv.nonlinear = nonlinear ? 1 : 0;
+    dv.kal_altitude = 0;
     dv.Sg0 = T.Sg0;
     dv.V0 = T.V0;
     dv.ne = T.ne;
@@ -561,6 +562,15 @@ lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3
     s->nn_total += T.nn;
     s->host_newer = true;
     s->tables_dirty = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_template_set_kal_direction(lbib_sim *s, int tid, int altitude) {
+    LBIB_GUARD(s);
+    if (tid < 0 || tid >= (int)s->tpl_dev.size()) return fail(s, LBIB_ERR_ID, "unknown template id");
+    s->tpl_dev[tid].kal_altitude = altitude ? 1 : 0;
+    s->tables_dirty = true;
+    s->fel_valid = false;
     return LBIB_OK;
 }
 

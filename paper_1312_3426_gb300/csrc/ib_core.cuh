@@ -269,12 +269,27 @@ __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, 
     const float inl = rsqrtf(dot(N, N));
     const float S = 0.5f * dot(N, N) * inl;
     const f3 G = (1.f / 3.f) * (B + C);  // centroid relative to a
-    const float cw = -T.kal * (S - S0) / S - T.kag * dSg;  // local + global area
     const f3 fv = (T.kv * dV * S * inl * (1.f / 3.f)) * N;  // volume, a third per vertex
     const f3 wa = -1.f * G, wb = B - G, wc = C - G;
-    F.add(tr.x, (cw * rsqrtf(dot(wa, wa))) * wa + fv);
-    F.add(tr.y, (cw * rsqrtf(dot(wb, wb))) * wb + fv);
-    F.add(tr.z, (cw * rsqrtf(dot(wc, wc))) * wc + fv);
+    if (!T.kal_altitude) {
+        const float cw = -T.kal * (S - S0) / S - T.kag * dSg;  // local + global area
+        F.add(tr.x, (cw * rsqrtf(dot(wa, wa))) * wa + fv);
+        F.add(tr.y, (cw * rsqrtf(dot(wb, wb))) * wb + fv);
+        F.add(tr.z, (cw * rsqrtf(dot(wc, wc))) * wc + fv);
+        return;
+    }
+    // local area along each vertex's altitude (from the foot on the opposite
+    // edge to the vertex), global area along centroid -> vertex
+    const float cl = -T.kal * (S - S0) / S, cg = -T.kag * dSg;
+    const f3 Z = mk(0.f, 0.f, 0.f);
+    auto alt = [](f3 p, f3 q, f3 r) {  // component of p - q orthogonal to r - q
+        const f3 e = r - q, d = p - q;
+        return d - (dot(d, e) / dot(e, e)) * e;
+    };
+    const f3 ha = alt(Z, B, C), hb = alt(B, C, Z), hc = alt(C, Z, B);
+    F.add(tr.x, (cl * rsqrtf(dot(ha, ha))) * ha + (cg * rsqrtf(dot(wa, wa))) * wa + fv);
+    F.add(tr.y, (cl * rsqrtf(dot(hb, hb))) * hb + (cg * rsqrtf(dot(wb, wb))) * wb + fv);
+    F.add(tr.z, (cl * rsqrtf(dot(hc, hc))) * hc + (cg * rsqrtf(dot(wc, wc))) * wc + fv);
 }
 
 // Coupling and Newton update of node i (global index) of object o under the

@@ -79,6 +79,7 @@ struct TplDev {
     int nn, nt, ne;
     float ks, kb, kal, kag, kv;
     int nonlinear;
+    int kal_altitude;  // local-area force along the altitudes (else centroid -> vertex)
     double Sg0, V0;
     const int4 *tri;
     const int4 *edge;

@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         "lbib_set_repulsion": (st, [P, P, P]),
         "lbib_set_inlet": (st, [P, P, P]),
         "lbib_set_solid": (st, [P, P, C.c_int64]),
+        "lbib_template_set_kal_direction": (st, [P, C.c_int, C.c_int]),
         "lbib_object_set_nodes": (st, [P, C.c_int, P, C.c_int]),
         "lbib_object_set_velocities": (st, [P, C.c_int, P, C.c_int]),
         "lbib_fluid_init": (st, [P]),
@@ -318,6 +319,10 @@ def lbib_set_repulsion(h, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
     a = _f64(obj, (3,))
     b = _f64(wall, (3,))
     _check(h, _lib.lbib_set_repulsion(h, _p(a), _p(b)))
+
+
+def lbib_template_set_kal_direction(h, tid, altitude):
+    _check(h, _lib.lbib_template_set_kal_direction(h, int(tid), int(bool(altitude))))
 
 
 def lbib_set_solid(h, mask):

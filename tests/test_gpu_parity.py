@@ -252,6 +252,27 @@ def test_membrane_forces_match_oracle(bit):
     assert np.abs(v - F).max() <= 2e-5 * scale, np.abs(v - F).max() / scale
 
 
+def test_local_area_along_altitudes_matches_oracle():
+    """The second local-area direction of Sec. 4, as test_membrane_forces_match_oracle."""
+    nodes, tris = mesh.biconcave(3)
+    sc = scenes.Scene("forces", 48, 48, 48, walls=False, friction=0.0, body_force=(0, 0, 0))
+    sc.templates.append(scenes.Template(nodes, tris, (8, 8, 8), kal=0.1, kag=0.4))
+    sc.objects.append(scenes.Obj(0, (24.2, 23.9, 24.4), (0.3, 0.9, -0.2)))
+    o = oracle.Oracle.from_scene(sc)
+    g = lbib.Sim.from_scene(sc)
+    o.template_set_kal_direction(0, True)
+    lbib.lbib_template_set_kal_direction(g.h, 0, True)
+    X, _ = o.read_nodes(0)
+    Xd = X + 0.15 * np.random.default_rng(7).standard_normal(X.shape)
+    o.object_set_nodes(0, Xd)
+    g.object_set_nodes(0, Xd)
+    F = o.membrane_forces(0, 4 | 8)
+    g.step(1)
+    _, v = g.read_nodes(0)
+    scale = np.abs(F).max()
+    assert np.abs(v - F).max() <= 2e-5 * scale, np.abs(v - F).max() / scale
+
+
 # ------------------------------------------------------------- conservation, read-outs
 
 def test_mass_conserved_fp64_reduction():
