@@ -137,6 +137,18 @@ LBIB_API lbib_status lbib_mesh_check(const double *nodes_xyz, int n_nodes, const
                                      double *theta0, double *S0, double *globals, int *n_edges, char *msg,
                                      int msg_cap);
 
+/* Mesh orientation (Sec. 5, mesh analysis: orientation check, repair,
+ * flip).  mode 0 reports in *changed how many triangles a repair would
+ * turn (0: the mesh is consistently ordered with AB x AC pointing inside);
+ * mode 1 repairs: the orientation is made consistent across shared edges
+ * and then chosen so that the triangles point inside (positive enclosed
+ * volume), which holds for concave meshes too; mode 2 flips every
+ * triangle.  out [n_tris][3] receives the resulting triangles (NULL:
+ * none).  Needs no GPU.  LBIB_ERR_MESH for a mesh that is not a closed
+ * orientable 2-manifold, LBIB_ERR_ARG for bad arguments. */
+LBIB_API lbib_status lbib_mesh_orient(const double *nodes_xyz, int n_nodes, const int32_t *tris, int n_tris, int mode,
+                                      int32_t *out, int *changed);
+
 /* Object (Sec. 5, adding of the object).  oid must equal the number of
  * objects added so far.  The template geometry is rotated by rotate[0]
  * about x, then rotate[1] about y, then rotate[2] about z (NULL = none),

@@ -530,6 +530,16 @@ lbib_status lbib_mesh_check(const double *xyz, int nn, const int32_t *tris, int 
     return report(LBIB_OK, "");
 }
 
+lbib_status lbib_mesh_orient(const double *xyz, int nn, const int32_t *tris, int nt, int mode, int32_t *out,
+                             int *changed) {
+    if (!xyz || !tris || nn < 4 || nt < 4 || mode < 0 || mode > 2) return LBIB_ERR_ARG;
+    int c = 0;
+    std::string err;
+    if (!orient_mesh(xyz, nn, tris, nt, mode, out, c, err)) return LBIB_ERR_MESH;
+    if (changed) *changed = c;
+    return LBIB_OK;
+}
+
 lbib_status lbib_object_add(lbib_sim *s, int oid, int tid, const double origin[3], const double rotate[3],
                             double mass) {
     LBIB_GUARD(s);

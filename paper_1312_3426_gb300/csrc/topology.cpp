@@ -165,6 +165,115 @@ bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, cons
     return true;
 }
 
+bool orient_mesh(const double *xyz, int nn, const int32_t *tris, int nt, int mode, int32_t *out, int &changed,
+                 std::string &err) {
+    changed = 0;
+    std::vector<int> t(tris, tris + 3 * (size_t)nt);
+    for (int v : t)
+        if (v < 0 || v >= nn) {
+            err = "triangle refers to a node id outside [0, n_nodes)";
+            return false;
+        }
+    std::vector<char> flip(nt, 0);
+    if (mode == 2) {
+        std::fill(flip.begin(), flip.end(), 1);
+    } else {
+        // undirected edge -> the (at most two) triangles using it
+        struct E {
+            uint64_t key;
+            int tri;
+        };
+        std::vector<E> es;
+        es.reserve(3 * (size_t)nt);
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < 3; ++k) {
+                uint32_t a = (uint32_t)t[3 * i + k], b = (uint32_t)t[3 * i + (k + 1) % 3];
+                if (a > b) std::swap(a, b);
+                es.push_back({((uint64_t)a << 32) | b, i});
+            }
+        std::sort(es.begin(), es.end(), [](const E &p, const E &q) { return p.key < q.key || (p.key == q.key && p.tri < q.tri); });
+        std::vector<std::vector<int>> nb(nt);
+        for (size_t k = 0; k < es.size();) {
+            size_t j = k;
+            while (j < es.size() && es[j].key == es[k].key) ++j;
+            if (j - k != 2) {
+                err = "an edge is not shared by exactly two triangles: the mesh is not a closed 2-manifold";
+                return false;
+            }
+            nb[es[k].tri].push_back(es[k + 1].tri);
+            nb[es[k + 1].tri].push_back(es[k].tri);
+            k = j;
+        }
+        // does triangle i (with its flip) traverse edge (a, b) in that order?
+        auto runs = [&](int i, int a, int b) {
+            for (int k = 0; k < 3; ++k) {
+                int p = t[3 * i + k], q = t[3 * i + (k + 1) % 3];
+                if (flip[i]) std::swap(p, q);
+                if (p == a && q == b) return true;
+            }
+            return false;
+        };
+        std::vector<char> seen(nt, 0);
+        for (int root = 0; root < nt; ++root) {
+            if (seen[root]) continue;
+            std::vector<int> comp{root}, queue{root};
+            seen[root] = 1;
+            for (size_t h = 0; h < queue.size(); ++h) {
+                const int i = queue[h];
+                for (int j : nb[i]) {
+                    // the shared edge must run in opposite directions
+                    int a = -1, b = -1;
+                    for (int k = 0; k < 3 && a < 0; ++k) {
+                        int p = t[3 * i + k], q = t[3 * i + (k + 1) % 3];
+                        if (flip[i]) std::swap(p, q);
+                        for (int m = 0; m < 3; ++m)
+                            if ((t[3 * j + m] == p || t[3 * j + m] == q) &&
+                                (t[3 * j + (m + 1) % 3] == p || t[3 * j + (m + 1) % 3] == q)) {
+                                a = p;
+                                b = q;
+                            }
+                    }
+                    if (!seen[j]) {
+                        seen[j] = 1;
+                        if (runs(j, a, b)) flip[j] ^= 1;
+                        comp.push_back(j);
+                        queue.push_back(j);
+                    } else if (runs(j, a, b)) {
+                        err = "the mesh is not orientable";
+                        return false;
+                    }
+                }
+            }
+            // inward: -(1/6) sum A.(B x C) > 0 with the first node of the component as origin
+            double v6 = 0.0;
+            const int o = t[3 * comp[0]];
+            for (int i : comp) {
+                int a = t[3 * i], b = t[3 * i + 1], c = t[3 * i + 2];
+                if (flip[i]) std::swap(b, c);
+                double A[3], B[3], Cc[3];
+                for (int k = 0; k < 3; ++k) {
+                    A[k] = xyz[3 * a + k] - xyz[3 * o + k];
+                    B[k] = xyz[3 * b + k] - xyz[3 * o + k];
+                    Cc[k] = xyz[3 * c + k] - xyz[3 * o + k];
+                }
+                v6 += A[0] * (B[1] * Cc[2] - B[2] * Cc[1]) + A[1] * (B[2] * Cc[0] - B[0] * Cc[2]) +
+                      A[2] * (B[0] * Cc[1] - B[1] * Cc[0]);
+            }
+            if (v6 > 0.0)
+                for (int i : comp) flip[i] ^= 1;
+        }
+    }
+    for (int i = 0; i < nt; ++i) {
+        changed += flip[i];
+        if (out) {
+            out[3 * i] = t[3 * i];
+            out[3 * i + 1] = flip[i] ? t[3 * i + 2] : t[3 * i + 1];
+            out[3 * i + 2] = flip[i] ? t[3 * i + 1] : t[3 * i + 2];
+        }
+    }
+    return true;
+}
+
 std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width) {
     const int n = (int)(nodes.size() / arity);
     int max_node = 0;

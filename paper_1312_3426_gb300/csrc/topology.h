@@ -29,4 +29,16 @@ std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, i
 bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
                     Topology &out, std::string &err);
 
+// Mesh orientation (Sec. 5, mesh analysis).  mode 0: report the triangles
+// that a repair would turn; 1: repair; 2: flip every triangle.  The repair
+// makes the orientation consistent across shared edges (breadth-first from
+// triangle 0 over each connected component) and then turns a component
+// whose divergence-theorem volume is negative, so that AB x AC points
+// inside; unlike a per-triangle test against the centroid this also holds
+// for concave meshes.  out: the resulting triangles (may alias nothing);
+// changed: number of triangles turned.  Returns false with err for a mesh
+// that is not a closed orientable 2-manifold.
+bool orient_mesh(const double *xyz, int nn, const int32_t *tris, int nt, int mode, int32_t *out, int &changed,
+                 std::string &err);
+
 }  // namespace lbib

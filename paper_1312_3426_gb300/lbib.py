@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         "lbib_set_inlet": (st, [P, P, P]),
         "lbib_set_solid": (st, [P, P, C.c_int64]),
         "lbib_template_set_kal_direction": (st, [P, C.c_int, C.c_int]),
+        "lbib_mesh_orient": (st, [P, C.c_int, P, C.c_int, C.c_int, P, C.POINTER(C.c_int)]),
         "lbib_object_set_nodes": (st, [P, C.c_int, P, C.c_int]),
         "lbib_object_set_velocities": (st, [P, C.c_int, P, C.c_int]),
         "lbib_fluid_init": (st, [P]),
@@ -319,6 +320,22 @@ def lbib_set_repulsion(h, obj=(0.0, 1.0, 0.0), wall=(0.0, 1.0, 0.0)):
     a = _f64(obj, (3,))
     b = _f64(wall, (3,))
     _check(h, _lib.lbib_set_repulsion(h, _p(a), _p(b)))
+
+
+MESH_CHECK, MESH_REPAIR, MESH_FLIP = 0, 1, 2
+
+
+def lbib_mesh_orient(nodes, tris, mode=MESH_REPAIR):
+    """(triangles after the operation, number of triangles turned)."""
+    load()
+    x = _f64(nodes).reshape(-1, 3)
+    t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros_like(t)
+    n = C.c_int(0)
+    st = _lib.lbib_mesh_orient(_p(x), len(x), _p(t), len(t), int(mode), _p(out), C.byref(n))
+    if st != LBIB_OK:
+        raise LbibError(st, "lbib_mesh_orient")
+    return out, n.value
 
 
 def lbib_template_set_kal_direction(h, tid, altitude):

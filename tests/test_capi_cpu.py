@@ -110,3 +110,41 @@ def test_server_host_logic_without_gpu():
         assert lbib.lbib_server_stats(srv)["advances"] == 0
     finally:
         lbib.lbib_server_destroy(srv)
+
+
+def test_mesh_orientation_check_repair_flip():
+    """Sec. 5 mesh analysis: a consistently inward mesh needs no change;
+    flipping every triangle is undone by the repair; a random subset of
+    turned triangles of a concave (biconcave) mesh is repaired exactly."""
+    for nodes, tris in (mesh.icosphere(2), mesh.biconcave(3)):
+        t = np.asarray(tris, dtype=np.int32)
+        _, n = lbib.lbib_mesh_orient(nodes, t, lbib.MESH_CHECK)
+        assert n == 0
+        fl, n = lbib.lbib_mesh_orient(nodes, t, lbib.MESH_FLIP)
+        assert n == len(t) and np.array_equal(fl[:, [0, 2, 1]], t)
+        rep, n = lbib.lbib_mesh_orient(nodes, fl, lbib.MESH_REPAIR)
+        assert n == len(t) and np.array_equal(rep, t)
+        rng = np.random.default_rng(5)
+        sel = rng.random(len(t)) < 0.3
+        bad = t.copy()
+        bad[sel] = bad[sel][:, [0, 2, 1]]
+        _, n = lbib.lbib_mesh_orient(nodes, bad, lbib.MESH_CHECK)
+        assert n == int(sel.sum())
+        rep, _ = lbib.lbib_mesh_orient(nodes, bad, lbib.MESH_REPAIR)
+        assert np.array_equal(rep, t)
+        lbib.lbib_mesh_check(nodes, rep)   # accepted as a template
+
+
+def test_mesh_orientation_rejects_open_mesh():
+    nodes, tris = mesh.icosphere(1)
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_mesh_orient(nodes, np.asarray(tris[1:], dtype=np.int32), lbib.MESH_REPAIR)
+
+
+def test_vtk_roundtrip(tmp_path):
+    from paper_1312_3426_gb300 import vtk
+    nodes, tris = mesh.biconcave(2)
+    p = tmp_path / "cell.vtk"
+    vtk.write_vtk(p, nodes * 8.0, tris, {"speed": np.arange(len(nodes), dtype=float)})
+    X, T = vtk.read_vtk(p)
+    assert np.array_equal(X, nodes * 8.0) and np.array_equal(T, tris)
