@@ -269,7 +269,10 @@ LBIB_API lbib_status lbib_objects_set_force(lbib_sim *sim, const double *f, int 
 LBIB_API lbib_status lbib_objects_analyze(lbib_sim *sim, double *out, int64_t cap);
 
 /* Per-phase timing with CUDA events on the streams the kernels run on.
- * While enabled, lbib_step records events around each kernel of each step.
+ * While enabled (on != 0), lbib_step records events around each kernel of
+ * every on-th step (on = 1: every step; the events themselves add a few
+ * microseconds to a timed step, so a sampling period keeps the run close
+ * to an untimed one).
  * lbib_profile_read waits for both streams and returns, since the last
  * enable: out[0] total ms and out[1] launches of the fluid kernel, out[2]
  * total ms and out[3] launches of the node-update kernel, out[4] total ms

@@ -722,7 +722,7 @@ static lbib_status prof_events(lbib_sim *s, std::vector<cudaEvent_t> &pool, size
 // Membrane forces of the current node positions, on stream `st`.
 static lbib_status launch_membrane_timed(lbib_sim *s, cudaStream_t st) {
     cudaEvent_t *ev = nullptr;
-    if (s->prof_on) {
+    if (s->prof_now) {
         lbib_status r = prof_events(s, s->prof_aux, s->prof_aux_used, 2, &ev);
         if (r != LBIB_OK) return r;
         LBIB_CUDA(s, cudaEventRecord(ev[0], st), "profile event");
@@ -747,6 +747,7 @@ lbib_status lbib_step(lbib_sim *s, int n) {
     lbib_status r = sim_prepare_step(s);
     if (r != LBIB_OK) return r;
     const bool objects = s->nn_total > 0 && !s->objs.empty();
+    s->prof_now = false;
     if (n > 0 && objects && !s->fel_valid && s->overlap) {
         r = launch_membrane_timed(s, s->stream);
         if (r != LBIB_OK) return r;
@@ -756,12 +757,15 @@ lbib_status lbib_step(lbib_sim *s, int n) {
         const int par = (int)(s->t & 1);
         if (s->since_mark >= ACTIVE_RESET_STEPS) LBIB_CUDA(s, sim_remark(s, s->stream), "active cells");
         s->since_mark++;
+        // timing events on sampled steps only: each event between two
+        // kernels costs a few microseconds of the step
+        s->prof_now = s->prof_on && (s->t % s->prof_every) == 0;
         if (objects && !s->overlap) {
             r = launch_membrane_timed(s, s->stream);
             if (r != LBIB_OK) return r;
         }
         cudaEvent_t *ev = nullptr;
-        if (s->prof_on) {
+        if (s->prof_now) {
             r = prof_events(s, s->prof_ev, s->prof_used, 3, &ev);
             if (r != LBIB_OK) return r;
             LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
@@ -781,6 +785,7 @@ lbib_status lbib_step(lbib_sim *s, int n) {
         s->t++;
         s->gmode = par;
     }
+    s->prof_now = false;
     if (!s->overlap) s->fel_valid = false;
     if (n > 0 && s->nn_total > 0) s->dev_newer = true;
     return LBIB_OK;
@@ -1083,6 +1088,7 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
 lbib_status lbib_profile_enable(lbib_sim *s, int on) {
     LBIB_GUARD(s);
     s->prof_on = on != 0;
+    s->prof_every = on > 1 ? on : 1;
     s->prof_used = 0;
     s->prof_aux_used = 0;
     return LBIB_OK;

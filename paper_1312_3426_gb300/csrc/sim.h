@@ -66,6 +66,8 @@ struct lbib_sim {
     size_t rep_bytes = 0;
 
     bool prof_on = false;        // per-phase CUDA-event timing
+    int prof_every = 1;          // ... of every prof_every-th step
+    bool prof_now = false;       // the step being enqueued is timed
     std::vector<cudaEvent_t> prof_ev;   // 3 per step on `stream`
     std::vector<cudaEvent_t> prof_aux;  // 2 per membrane launch on `aux`
     size_t prof_used = 0, prof_aux_used = 0;

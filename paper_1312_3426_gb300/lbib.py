@@ -306,7 +306,8 @@ def lbib_get_tuning(h, key):
 
 
 def lbib_profile_enable(h, on=True):
-    _check(h, _lib.lbib_profile_enable(h, int(bool(on))))
+    """on: False/0 off, True/1 every step, n > 1 every n-th step."""
+    _check(h, _lib.lbib_profile_enable(h, int(on)))
 
 
 def lbib_profile_read(h):
