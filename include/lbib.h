@@ -257,7 +257,8 @@ LBIB_API lbib_status lbib_set_populations(lbib_sim *sim, const double *h, int64_
 
 /* Object analysis (Sec. 5): out[14] = origin (mean of nodes) [3], bounds
  * xmin,xmax,ymin,ymax,zmin,zmax [6], volume, surface area, mean node
- * velocity [3].  Volume and area are FP64 sums on the GPU. */
+ * velocity [3].  Sums are error-free FP32 pairs on the GPU over positions
+ * relative to the first node, finished in FP64. */
 LBIB_API lbib_status lbib_object_analyze(lbib_sim *sim, int oid, double out[14]);
 
 /* Batched forms for a per-step host loop (the paper's main loop sets inputs

@@ -102,11 +102,7 @@ void rotation_zyx(const double r[3], double R[3][3]) {
 namespace lbib {
 
 // Status word -> sticky error.
-lbib_status sim_check_status(lbib_sim *s) {
-    uint32_t st = 0;
-    cudaError_t e = cudaMemcpyAsync(&st, s->d.status, 4, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+static lbib_status apply_status(lbib_sim *s, uint32_t st) {
     if (st & ST_TIMEOUT) {
         s->sticky = LBIB_ERR_TIMEOUT;
         s->err = "a bounded device-side wait gave up";
@@ -118,6 +114,14 @@ lbib_status sim_check_status(lbib_sim *s) {
         s->err = (st & ST_UNSTABLE) ? "fluid became unstable (NaN or |u| > 0.3)" : "a node position became non-finite";
     }
     return s->sticky;
+}
+
+// Waits for the stream and folds the device status word into the sticky error.
+lbib_status sim_check_status(lbib_sim *s) {
+    cudaError_t e = cudaMemcpyAsync(s->status_pinned, s->d.status, 4, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+    return apply_status(s, *s->status_pinned);
 }
 
 lbib_status sim_download_nodes(lbib_sim *s) {
@@ -194,9 +198,21 @@ lbib_status sim_upload(lbib_sim *s) {
         s->fel_valid = false;
     }
     if (s->fext_dirty && !s->objs.empty()) {
-        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext.data(), s->fext.size() * sizeof(float),
-                                     cudaMemcpyHostToDevice, s->stream), "object forces");
-        LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "object forces");
+        // asynchronous upload through a page-locked staging buffer; the
+        // buffer is refilled only once the previous upload out of it is done
+        const size_t n = s->fext.size();
+        LBIB_CUDA(s, cudaEventSynchronize(s->ev_fext), "object forces");
+        if (n > s->fext_pinned_cap) {
+            if (s->fext_pinned) cudaFreeHost(s->fext_pinned);
+            s->fext_pinned = nullptr;
+            s->fext_pinned_cap = 0;
+            LBIB_CUDA(s, cudaMallocHost(&s->fext_pinned, n * sizeof(float)), "object force staging");
+            s->fext_pinned_cap = n;
+        }
+        std::memcpy(s->fext_pinned, s->fext.data(), n * sizeof(float));
+        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext_pinned, n * sizeof(float), cudaMemcpyHostToDevice, s->stream),
+                  "object forces");
+        LBIB_CUDA(s, cudaEventRecord(s->ev_fext, s->stream), "object forces");
         s->fext_dirty = false;
     }
     if (s->host_newer) {
@@ -364,8 +380,12 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_nodes, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_membrane, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fext, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->status_pinned, 64);
     if (e != cudaSuccess) {
         if (s->ev_nodes) cudaEventDestroy(s->ev_nodes);
+        if (s->ev_membrane) cudaEventDestroy(s->ev_membrane);
+        if (s->ev_fext) cudaEventDestroy(s->ev_fext);
         if (s->aux) cudaStreamDestroy(s->aux);
         cudaFree(s->fluid_mem);
         delete s;
@@ -385,6 +405,9 @@ void lbib_destroy(lbib_sim *s) {
     }
     if (s->ev_nodes) cudaEventDestroy(s->ev_nodes);
     if (s->ev_membrane) cudaEventDestroy(s->ev_membrane);
+    if (s->ev_fext) cudaEventDestroy(s->ev_fext);
+    if (s->fext_pinned) cudaFreeHost(s->fext_pinned);
+    if (s->status_pinned) cudaFreeHost(s->status_pinned);
     for (auto &t : s->tpl_mem) cudaFree(t);
     if (s->d_tpl) cudaFree(s->d_tpl);
     if (s->d_obj) cudaFree(s->d_obj);
@@ -1035,8 +1058,10 @@ lbib_status lbib_objects_analyze(lbib_sim *s, double *out, int64_t cap) {
     LBIB_CUDA(s, launch_analyze(s->d, -1, s->d_analyze, s->stream), "analyze");
     LBIB_CUDA(s, cudaMemcpyAsync(out, s->d_analyze, (size_t)nobj * 14 * sizeof(double), cudaMemcpyDeviceToHost,
                                  s->stream), "analyze");
+    // the status word comes back with the analysis: one wait for both
+    LBIB_CUDA(s, cudaMemcpyAsync(s->status_pinned, s->d.status, 4, cudaMemcpyDeviceToHost, s->stream), "analyze");
     LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "analyze");
-    return sim_check_status(s);
+    return apply_status(s, *s->status_pinned);
 }
 
 lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {

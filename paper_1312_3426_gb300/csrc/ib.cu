@@ -202,70 +202,89 @@ cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st) {
 }
 
 // Object analysis (Sec. 5): mean position, bounds, volume, area, mean
-// velocity of one object, all in FP64 (a read-out, not part of the step).
-__global__ void k_analyze(SimDev s, int oid, double *out) {
+// velocity of one object (a read-out, not part of the step).  One block per
+// object.  Sums are taken as error-free FP32 pairs over
+// positions relative to the object's first node (hi + lo differences),
+// reduced in a fixed order (so one object's analysis is bit-identical
+// alone and in the all-objects launch) and finished in FP64.
+__global__ void __launch_bounds__(256) k_analyze(SimDev s, int oid, double *out) {
     if (oid < 0) {
         oid = blockIdx.x;
         out += 14 * (size_t)oid;
     }
     const ObjDev ob = s.obj[oid];
-    const TplDev T = s.tpl[ob.tid];
-    const int NN = s.nn_total;
-    auto X = [&](int k, int i) { return (double)s.Xh[k * NN + i] + (double)s.Xl[k * NN + i]; };
-    auto V = [&](int k, int i) { return (double)s.Vh[k * NN + i] + (double)s.Vl[k * NN + i]; };
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // sx sy sz vx vy vz S V
-    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    const TplDev &T = s.tpl[ob.tid];
+    const int NN = s.nn_total, f0 = ob.first;
+    const float bh[3] = {s.Xh[f0], s.Xh[NN + f0], s.Xh[2 * NN + f0]};
+    const float bl[3] = {s.Xl[f0], s.Xl[NN + f0], s.Xl[2 * NN + f0]};
+    auto rel = [&](int k, int p) {  // node p relative to the first node
+        return (s.Xh[k * NN + f0 + p] - bh[k]) + (s.Xl[k * NN + f0 + p] - bl[k]);
+    };
+    df acc[8] = {};  // sum of relative x, y, z; of v x, y, z; area; 6 x volume
+    float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
     for (int p = threadIdx.x; p < ob.nn; p += blockDim.x) {
-        const int i = ob.first + p;
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double q = X(k, i);
-            acc[k] += q;
-            mn[k] = fmin(mn[k], q);
-            mx[k] = fmax(mx[k], q);
-            acc[3 + k] += V(k, i);
+            const float q = rel(k, p);
+            acc[k] = df_add_f(acc[k], q);
+            mn[k] = fminf(mn[k], q);
+            mx[k] = fmaxf(mx[k], q);
+            acc[3 + k] = df_add(acc[3 + k], df{s.Vh[k * NN + f0 + p], s.Vl[k * NN + f0 + p]});
         }
     }
-    const int f0 = ob.first;
     for (int t = threadIdx.x; t < T.nt; t += blockDim.x) {
         const int4 tr = T.tri[t];
-        double a[3], b[3], c[3];
-        for (int k = 0; k < 3; ++k) {
-            const double o = X(k, f0);
-            a[k] = X(k, f0 + tr.x) - o;
-            b[k] = X(k, f0 + tr.y) - o;
-            c[k] = X(k, f0 + tr.z) - o;
-        }
-        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-        const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-        acc[6] += 0.5 * sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        acc[7] += -(a[0] * n[0] + a[1] * n[1] + a[2] * n[2]) / 6.0;
+        const f3 A = mk(rel(0, tr.x), rel(1, tr.x), rel(2, tr.x));
+        const f3 B = mk(rel(0, tr.y), rel(1, tr.y), rel(2, tr.y)) - A;
+        const f3 Cc = mk(rel(0, tr.z), rel(1, tr.z), rel(2, tr.z)) - A;
+        const f3 N = cross(B, Cc);
+        acc[6] = df_add_f(acc[6], 0.5f * sqrtf(dot(N, N)));
+        acc[7] = df_add_f(acc[7], dot(A, N));
     }
-    __shared__ double sacc[8][256];
-    __shared__ double smn[3][256], smx[3][256];
-    for (int k = 0; k < 8; ++k) sacc[k][threadIdx.x] = acc[k];
-    for (int k = 0; k < 3; ++k) {
-        smn[k][threadIdx.x] = mn[k];
-        smx[k][threadIdx.x] = mx[k];
+    // fixed-order reduction: warp shuffles, then warp 0 over the warps
+    __shared__ df wacc[8][8];
+    __shared__ float wmn[3][8], wmx[3][8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = warp_sum_df(acc[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    if (lane == 0) {
+        for (int k = 0; k < 8; ++k) wacc[k][w] = acc[k];
+        for (int k = 0; k < 3; ++k) {
+            wmn[k][w] = mn[k];
+            wmx[k][w] = mx[k];
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int t = 1; t < blockDim.x; ++t) {
-            for (int k = 0; k < 8; ++k) sacc[k][0] += sacc[k][t];
-            for (int k = 0; k < 3; ++k) {
-                smn[k][0] = fmin(smn[k][0], smn[k][t]);
-                smx[k][0] = fmax(smx[k][0], smx[k][t]);
-            }
+        const int nw = (int)(blockDim.x >> 5);
+        double tot[8];
+        for (int k = 0; k < 8; ++k) {
+            df t = wacc[k][0];
+            for (int j = 1; j < nw; ++j) t = df_add(t, wacc[k][j]);
+            tot[k] = (double)t.hi + (double)t.lo;
         }
         const double inv = 1.0 / ob.nn;
-        for (int k = 0; k < 3; ++k) out[k] = sacc[k][0] * inv;
         for (int k = 0; k < 3; ++k) {
-            out[3 + 2 * k] = smn[k][0];
-            out[4 + 2 * k] = smx[k][0];
+            const double base = (double)bh[k] + (double)bl[k];
+            float lo = wmn[k][0], hi = wmx[k][0];
+            for (int j = 1; j < nw; ++j) {
+                lo = fminf(lo, wmn[k][j]);
+                hi = fmaxf(hi, wmx[k][j]);
+            }
+            out[k] = base + tot[k] * inv;
+            out[3 + 2 * k] = base + (double)lo;
+            out[4 + 2 * k] = base + (double)hi;
+            out[11 + k] = tot[3 + k] * inv;
         }
-        out[9] = sacc[7][0];
-        out[10] = sacc[6][0];
-        for (int k = 0; k < 3; ++k) out[11 + k] = sacc[3 + k][0] * inv;
+        out[9] = -tot[7] / 6.0;
+        out[10] = tot[6];
     }
 }
 

@@ -41,6 +41,10 @@ struct lbib_sim {
     lbib::ObjDev *d_obj = nullptr;
     lbib::TplDev *d_tpl = nullptr;
     std::vector<float> fext;     // [nobj][3]
+    float *fext_pinned = nullptr;      // page-locked staging of fext for asynchronous uploads
+    size_t fext_pinned_cap = 0;
+    cudaEvent_t ev_fext = nullptr;     // the last upload out of the staging buffer
+    uint32_t *status_pinned = nullptr; // page-locked copy of the device status word
     std::vector<double> masses;
     float *d_fext = nullptr;
     int cluster = 1;             // thread blocks per object in the membrane kernel
