@@ -123,7 +123,9 @@ struct BatchPlan {
     }
 };
 
+// One plan per process; lbib_batch_step calls are serialised on it.
 static BatchPlan g_plan;
+static std::mutex g_plan_mu;
 
 // Fluid kernel variant of a simulation: 2 * precision + BC (obstacles or an
 // inlet) for the one-cell-per-thread kernels; 6 / 7 for the two-cells
@@ -145,12 +147,8 @@ static bool plan_matches(lbib_sim *const *sims, int n, int cluster) {
 }
 
 static cudaError_t set_membrane_attrs(size_t smem) {
-    static size_t configured = 0;
-    if (smem <= configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_batch_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_membrane, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess) configured = smem;
-    return e;
+    static SmemAttr attr;
+    return attr.ensure((const void *)k_batch_membrane, smem, true);
 }
 
 static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStream_t st) {
@@ -309,6 +307,7 @@ using namespace lbib;
 
 extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps) {
     if (!sims || n <= 0 || n_steps < 0) return LBIB_ERR_ARG;
+    std::lock_guard<std::mutex> plan_lock(g_plan_mu);
     for (int i = 0; i < n; ++i) {
         if (!sims[i]) return LBIB_ERR_ARG;
         if (sims[i]->sticky != LBIB_OK) return sims[i]->sticky;

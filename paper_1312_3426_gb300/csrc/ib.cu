@@ -25,14 +25,9 @@ cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max
                             cudaStream_t st) {
     if (s.nobj == 0) return cudaSuccess;
     const size_t smem = ib_smem_bytes(max_nodes);
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_membrane, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static SmemAttr attr;
+    cudaError_t ea = attr.ensure((const void *)k_membrane, smem, true);
+    if (ea != cudaSuccess) return ea;
     cudaLaunchConfig_t cfg = {};
     const int n_clusters = (max_clusters > 0 && max_clusters < s.nobj) ? max_clusters : s.nobj;
     cfg.gridDim = dim3((unsigned)(n_clusters * cluster));
@@ -171,12 +166,8 @@ cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st) {
     k_rep_pairs<<<dim3((s.nobj + 255) / 256, s.nobj), 256, 0, st>>>(s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = (size_t)9 * max_nodes * sizeof(float);
-    static size_t configured = 0;
-    if (smem > configured) {
-        e = cudaFuncSetAttribute(k_rep_forces, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static SmemAttr attr;
+    if ((e = attr.ensure((const void *)k_rep_forces, smem, false)) != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

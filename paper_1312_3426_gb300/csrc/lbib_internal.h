@@ -30,6 +30,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <mutex>
 #include <stdint.h>
 
 #include "lbib.h"
@@ -163,6 +165,26 @@ __device__ __forceinline__ bool solid_bit(const SimDev &s, int f) {
     return (__ldg(s.solid + (f >> 5)) >> (f & 31)) & 1u;
 }
 #endif
+
+// Raises a kernel's dynamic shared-memory limit (and, for cluster kernels,
+// allows non-portable cluster sizes) once per device and size; safe to call
+// from several threads.
+struct SmemAttr {
+    std::mutex mu;
+    size_t done[64] = {};
+    cudaError_t ensure(const void *fn, size_t bytes, bool cluster) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lock(mu);
+        if (bytes <= done[dev] && done[dev] != 0) return cudaSuccess;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e == cudaSuccess && cluster) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) done[dev] = bytes > 0 ? bytes : 1;
+        return e;
+    }
+};
 
 // ---- launchers (fluid.cu) -------------------------------------------------
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);
