@@ -11,14 +11,16 @@
 namespace lbib {
 
 // Storage of one population.  FP32 is stored as is.  FP16/BF16 store the
-// deviation times 2^s with stochastic rounding: a random integer below the
-// weight of the first dropped bit is added to the FP32 bit pattern, which is
-// then truncated, so the stored value is unbiased.  Rounding to nearest
-// would turn the per-step forcing increment, which is far below one unit in
-// the last place of a 16-bit number once the flow has built up, into a
-// systematic error.  The random bits come from a counter-based hash of
-// (cell, step) stepped by a linear congruential generator across the
-// directions, so results are reproducible.
+// deviation times 2^s with stochastic rounding: the conversion rounds up
+// with probability equal to the dropped fraction of a unit in the last
+// place, so the stored value is unbiased.  Rounding to nearest would turn
+// the per-step forcing increment, which is far below one unit in the last
+// place of a 16-bit number once the flow has built up, into a systematic
+// error.  The rounding is the hardware's (cvt.rs, which converts two FP32
+// numbers into a packed pair with 32 random bits); the random bits come
+// from a counter-based hash of (cell, step) stepped by a linear
+// congruential generator across the directions, so results are
+// reproducible.
 //
 // PopIO::ld reads a deviation (read-outs and reductions); Raw below is the
 // step kernel's access to the stored numbers themselves.
@@ -76,23 +78,48 @@ __device__ __forceinline__ Nbr neighbours(const SimDev &s, int x, int y, int z) 
     return n;
 }
 
-// Pull the population of direction Q arriving at cell f.
+// Two FP32 numbers to a packed pair of 16-bit numbers (lo in the low half)
+// with stochastic rounding; r supplies the random bits of both.  Beyond the
+// largest finite number the result saturates.
+template <typename T>
+struct Pack2;
+template <>
+struct Pack2<__half> {
+    static __device__ __forceinline__ uint32_t rs(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+};
+template <>
+struct Pack2<__nv_bfloat16> {
+    static __device__ __forceinline__ uint32_t rs(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+};
+
 // Raw storage access for the step kernel: the stored number as float (the
-// deviation times 2^s for FP16/BF16), and the store of such a number with
-// the stochastic rounding of PopIO (low bits of rnd).
+// deviation times 2^s for FP16/BF16), and the store of two such numbers at
+// two addresses, rounded together with the random bits r.
 template <typename T>
 struct Raw;
 template <>
 struct Raw<float> {
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float v, uint32_t) { __stcs(p, v); }
+    static __device__ __forceinline__ void st2(float *p, float *q, float a, float b, uint32_t) {
+        __stcs(p, a);
+        __stcs(q, b);
+    }
 };
 template <>
 struct Raw<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st(__half *p, float v, uint32_t rnd) {
-        const __half h = __float2half_rz(__uint_as_float(__float_as_uint(v) + (rnd & 0x1fffu)));
-        __stcs((unsigned short *)p, __half_as_ushort(h));
+    static __device__ __forceinline__ void st2(__half *p, __half *q, float a, float b, uint32_t r) {
+        const uint32_t d = Pack2<__half>::rs(a, b, r);
+        __stcs((unsigned short *)p, (unsigned short)d);
+        __stcs((unsigned short *)q, (unsigned short)(d >> 16));
     }
 };
 template <>
@@ -100,9 +127,10 @@ struct Raw<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
         return __uint_as_float((uint32_t)__ldg((const unsigned short *)p) << 16);
     }
-    // round toward zero of the randomised pattern is its upper half
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v, uint32_t rnd) {
-        __stcs((unsigned short *)p, (unsigned short)((__float_as_uint(v) + (rnd & 0xffffu)) >> 16));
+    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, __nv_bfloat16 *q, float a, float b, uint32_t r) {
+        const uint32_t d = Pack2<__nv_bfloat16>::rs(a, b, r);
+        __stcs((unsigned short *)p, (unsigned short)d);
+        __stcs((unsigned short *)q, (unsigned short)(d >> 16));
     }
 };
 
@@ -126,22 +154,31 @@ __device__ __forceinline__ float pull(const SimDev &s, const T *__restrict__ src
     return Raw<T>::ld(src + (uint32_t)Q * nfp + (uint32_t)g);
 }
 
-// Per-cell constants of the collision (see fluid_cell) and the constants
-// of the simulation.
-struct Coll {
-    float K, r45, uG3, om3rho, ux, uy, uz, Gx, Gy, Gz;
-};
-struct CollK {
-    float om, fp, c1, fp3;
-};
-
 // BGK + Guo update of the opposite pair (Q, Q+1) (e_{Q+1} = -e_Q, same
 // weight w), from the split into the parts even and odd in e:
-//   out_{Q/Q+1} = (1 - omega) h + w [A +- B],
+//   out_{Q/Q+1} = (1 - omega) h + w 2^s [A +- B],
 //   A = omega (K + 4.5 rho (e.u)^2) + fpre (9 (e.u)(e.G) - 3 u.G),
 //   B = 3 omega rho (e.u) + 3 fpre (e.G),   K = drho - 1.5 rho u.u,
 // which is h - omega (h - h_eq) + fpre w [3 (e - u) + 9 (e.u) e].G written
-// out for both directions.  wsc = w 2^s (raw storage units).
+// out for both directions (2^s: raw storage units).  Per cell the
+// constants Kb = omega K - 3 fpre u.G and Rb = 3 omega rho are formed once;
+// per weight class (wsc = w 2^s) Kc = wsc Kb, Rc = wsc Rb, R15 = 1.5 Rc
+// and Gc = 3 fpre wsc G.  As 4.5 omega rho = 1.5 Rb, a pair then costs
+//   w 2^s B = Rc (e.u) + e.Gc,   w 2^s A = Kc + (e.u) (R15 (e.u) + 3 e.Gc).
+// A does not reuse the rounded B (A = Kc + 1.5 (e.u) (B + e.Gc) is the same
+// number in exact arithmetic): that product of e.u with a rounded multiple
+// of e.u has a rounding error of one sign, which drifted the total mass by
+// about 1e-9 per cell and step with 16-bit storage.
+struct Coll {
+    float ux, uy, uz, Gx, Gy, Gz, Kb, Rb;
+};
+struct Cls {
+    float K, R, R15, gx, gy, gz;
+};
+struct CollK {
+    float om, c1, fp3, om3;
+};
+
 // e component E (-1, 0, 1) times v without a multiply; the zero is -0.0f,
 // which the compiler drops from a sum (x + -0 = x for every x), so the
 // dot products and moment sums below carry only their non-zero terms.
@@ -183,24 +220,28 @@ __device__ __forceinline__ Moments moments19(const float (&h)[NQ]) {
     return m;
 }
 
-// (A + B, A - B) times w 2^s for the opposite pair (Q, Q+1) of one cell.
+// The constants of one weight class (wsc = w 2^s).
+__device__ __forceinline__ Cls make_cls(const Coll &c, const CollK &k, float wsc) {
+    const float g = k.fp3 * wsc, R = wsc * c.Rb;
+    return Cls{wsc * c.Kb, R, 1.5f * R, g * c.Gx, g * c.Gy, g * c.Gz};
+}
+
+// w 2^s (A + B, A - B) for the opposite pair (Q, Q+1) of one cell.
 template <int Q>
-__device__ __forceinline__ float2 pair_terms(const Coll &c, const CollK &k, float wsc) {
+__device__ __forceinline__ float2 pair_terms(const Coll &c, const Cls &w) {
     const float eu = edot<Q>(c.ux, c.uy, c.uz);
-    const float eG = edot<Q>(c.Gx, c.Gy, c.Gz);
-    const float t = fmaf(c.r45, eu * eu, c.K);
-    const float fs = fmaf(9.0f * eu, eG, -c.uG3);
-    const float A = wsc * fmaf(k.om, t, k.fp * fs);
-    const float B = wsc * fmaf(c.om3rho, eu, k.fp3 * eG);
+    const float eg = edot<Q>(w.gx, w.gy, w.gz);
+    const float B = fmaf(w.R, eu, eg);
+    const float A = fmaf(eu, fmaf(w.R15, eu, 3.0f * eg), w.K);
     return make_float2(A + B, A - B);
 }
 
 template <typename T, int Q>
 __device__ __forceinline__ void collide_pair(T *__restrict__ dst, uint32_t nfp, uint32_t f, float hq, float ho,
-                                             const Coll &c, const CollK &k, float wsc, uint32_t rnd) {
-    const float2 ab = pair_terms<Q>(c, k, wsc);
-    Raw<T>::st(dst + (uint32_t)Q * nfp + f, fmaf(k.c1, hq, ab.x), rnd);
-    Raw<T>::st(dst + (uint32_t)(Q + 1) * nfp + f, fmaf(k.c1, ho, ab.y), rnd >> 16);
+                                             const Coll &c, const CollK &k, const Cls &w, uint32_t rnd) {
+    const float2 ab = pair_terms<Q>(c, w);
+    Raw<T>::st2(dst + (uint32_t)Q * nfp + f, dst + (uint32_t)(Q + 1) * nfp + f, fmaf(k.c1, hq, ab.x),
+                fmaf(k.c1, ho, ab.y), rnd);
 }
 
 // Collision constants of one cell from the raw moments.
@@ -219,19 +260,18 @@ __device__ __forceinline__ Coll make_coll(const SimDev &s, const CollK &k, float
     c.Gz = Gz;
     usq = c.ux * c.ux + c.uy * c.uy + c.uz * c.uz;
     const float uG = c.ux * Gx + c.uy * Gy + c.uz * Gz;
-    c.K = fmaf(-1.5f * rho, usq, drho);
-    c.r45 = 4.5f * rho;
-    c.uG3 = 3.0f * uG;
-    c.om3rho = 3.0f * k.om * rho;
+    const float K = fmaf(-1.5f * rho, usq, drho);
+    c.Kb = fmaf(k.om, K, -k.fp3 * uG);
+    c.Rb = k.om3 * rho;
     return c;
 }
 
 __device__ __forceinline__ CollK make_collk(const SimDev &s) {
     CollK k;
     k.om = s.omega;
-    k.fp = s.fpre;
     k.c1 = 1.0f - s.omega;
     k.fp3 = 3.0f * s.fpre;
+    k.om3 = 3.0f * s.omega;
     return k;
 }
 
@@ -315,26 +355,34 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
     float rho, usq;
     const Coll c = make_coll(s, k, m.r, m.x, m.y, m.z, Gx, Gy, Gz, rho, usq);
     const float sc = s.scale;
-    const float wsc0 = (float)d3q19_w(0) * sc, wsc1 = (float)d3q19_w(1) * sc, wsc2 = (float)d3q19_w(7) * sc;
+    const float wsc0 = (float)d3q19_w(0) * sc;
+    const Cls w1 = make_cls(c, k, (float)d3q19_w(1) * sc);
+    const Cls w2 = make_cls(c, k, (float)d3q19_w(7) * sc);
 
-    // 16 random bits per population for FP16/BF16 (one step of a linear
-    // congruential generator per pair of populations)
+    // 32 random bits per rounded pair of populations for FP16/BF16 (one
+    // step of a linear congruential generator each)
     uint32_t rng = (sizeof(T) == 2) ? mix32(f ^ step_seed) : 0u;
     auto next = [&]() -> uint32_t {
         if (sizeof(T) != 2) return 0u;
         rng = rng * 747796405u + 2891336453u;
         return rng ^ (rng >> 15);
     };
-    Raw<T>::st(dst + f, fmaf(k.c1, h[0], wsc0 * fmaf(k.om, c.K, -k.fp * c.uG3)), next());
-    collide_pair<T, 1>(dst, nfp, f, h[1], h[2], c, k, wsc1, next());
-    collide_pair<T, 3>(dst, nfp, f, h[3], h[4], c, k, wsc1, next());
-    collide_pair<T, 5>(dst, nfp, f, h[5], h[6], c, k, wsc1, next());
-    collide_pair<T, 7>(dst, nfp, f, h[7], h[8], c, k, wsc2, next());
-    collide_pair<T, 9>(dst, nfp, f, h[9], h[10], c, k, wsc2, next());
-    collide_pair<T, 11>(dst, nfp, f, h[11], h[12], c, k, wsc2, next());
-    collide_pair<T, 13>(dst, nfp, f, h[13], h[14], c, k, wsc2, next());
-    collide_pair<T, 15>(dst, nfp, f, h[15], h[16], c, k, wsc2, next());
-    collide_pair<T, 17>(dst, nfp, f, h[17], h[18], c, k, wsc2, next());
+    const float out0 = fmaf(k.c1, h[0], wsc0 * c.Kb);
+    if constexpr (sizeof(T) == 2) {  // the rest population alone: the high half is discarded
+        const uint32_t d = Pack2<T>::rs(out0, 0.0f, next());
+        __stcs((unsigned short *)(dst + f), (unsigned short)d);
+    } else {
+        __stcs((float *)(dst + f), out0);
+    }
+    collide_pair<T, 1>(dst, nfp, f, h[1], h[2], c, k, w1, next());
+    collide_pair<T, 3>(dst, nfp, f, h[3], h[4], c, k, w1, next());
+    collide_pair<T, 5>(dst, nfp, f, h[5], h[6], c, k, w1, next());
+    collide_pair<T, 7>(dst, nfp, f, h[7], h[8], c, k, w2, next());
+    collide_pair<T, 9>(dst, nfp, f, h[9], h[10], c, k, w2, next());
+    collide_pair<T, 11>(dst, nfp, f, h[11], h[12], c, k, w2, next());
+    collide_pair<T, 13>(dst, nfp, f, h[13], h[14], c, k, w2, next());
+    collide_pair<T, 15>(dst, nfp, f, h[15], h[16], c, k, w2, next());
+    collide_pair<T, 17>(dst, nfp, f, h[17], h[18], c, k, w2, next());
 
     if (active) s.ufield[f] = make_float4(c.ux, c.uy, c.uz, rho);
     if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
@@ -357,23 +405,11 @@ struct Half2Bits<__half> {
     static __device__ __forceinline__ float hi(uint32_t u) {
         return __half2float(__ushort_as_half((unsigned short)(u >> 16)));
     }
-    // stochastic rounding of two values (as Raw<__half>::st), 13 random
-    // bits each from the two halves of r
-    static __device__ __forceinline__ uint32_t pack(float a, float b, uint32_t r) {
-        const __half ha = __float2half_rz(__uint_as_float(__float_as_uint(a) + (r & 0x1fffu)));
-        const __half hb = __float2half_rz(__uint_as_float(__float_as_uint(b) + ((r >> 16) & 0x1fffu)));
-        return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
-    }
 };
 template <>
 struct Half2Bits<__nv_bfloat16> {
     static __device__ __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
     static __device__ __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
-    static __device__ __forceinline__ uint32_t pack(float a, float b, uint32_t r) {
-        const uint32_t ba = __float_as_uint(a) + (r & 0xffffu);
-        const uint32_t bb = __float_as_uint(b) + (r >> 16);
-        return (ba >> 16) | (bb & 0xffff0000u);
-    }
 };
 
 // The pair of direction Q arriving at cells f, f+1 (low half: cell f).
@@ -410,17 +446,17 @@ __device__ __forceinline__ Moments moments_half(const uint32_t (&P)[NQ], bool hi
 
 template <typename T, int Q>
 __device__ __forceinline__ void collide2(uint32_t *__restrict__ dst, uint32_t nfp2, uint32_t f2, uint32_t Pq,
-                                         uint32_t Po, const Coll &a, const Coll &b, const CollK &k, float wsc,
-                                         uint32_t &rng) {
-    const float2 ta = pair_terms<Q>(a, k, wsc), tb = pair_terms<Q>(b, k, wsc);
+                                         uint32_t Po, const Coll &a, const Coll &b, const CollK &k, const Cls &wa,
+                                         const Cls &wb, uint32_t &rng) {
+    const float2 ta = pair_terms<Q>(a, wa), tb = pair_terms<Q>(b, wb);
     rng = rng * 747796405u + 2891336453u;
     const uint32_t r1 = rng ^ (rng >> 15);
     rng = rng * 747796405u + 2891336453u;
     const uint32_t r2 = rng ^ (rng >> 15);
     __stcs((unsigned int *)(dst + (uint32_t)Q * nfp2 + f2),
-           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(Pq), ta.x), fmaf(k.c1, Half2Bits<T>::hi(Pq), tb.x), r1));
+           Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(Pq), ta.x), fmaf(k.c1, Half2Bits<T>::hi(Pq), tb.x), r1));
     __stcs((unsigned int *)(dst + (uint32_t)(Q + 1) * nfp2 + f2),
-           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(Po), ta.y), fmaf(k.c1, Half2Bits<T>::hi(Po), tb.y), r2));
+           Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(Po), ta.y), fmaf(k.c1, Half2Bits<T>::hi(Po), tb.y), r2));
 }
 
 template <typename T>
@@ -463,19 +499,22 @@ __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uin
     const uint32_t nfp2 = nfp / 2, f2 = f / 2;
     uint32_t rng = mix32(f ^ step_seed);
     rng = rng * 747796405u + 2891336453u;
-    __stcs((unsigned int *)(dst + f2),
-           Half2Bits<T>::pack(fmaf(k.c1, Half2Bits<T>::lo(P[0]), wsc0 * fmaf(k.om, a.K, -k.fp * a.uG3)),
-                              fmaf(k.c1, Half2Bits<T>::hi(P[0]), wsc0 * fmaf(k.om, b.K, -k.fp * b.uG3)),
-                              rng ^ (rng >> 15)));
-    collide2<T, 1>(dst, nfp2, f2, P[1], P[2], a, b, k, wsc1, rng);
-    collide2<T, 3>(dst, nfp2, f2, P[3], P[4], a, b, k, wsc1, rng);
-    collide2<T, 5>(dst, nfp2, f2, P[5], P[6], a, b, k, wsc1, rng);
-    collide2<T, 7>(dst, nfp2, f2, P[7], P[8], a, b, k, wsc2, rng);
-    collide2<T, 9>(dst, nfp2, f2, P[9], P[10], a, b, k, wsc2, rng);
-    collide2<T, 11>(dst, nfp2, f2, P[11], P[12], a, b, k, wsc2, rng);
-    collide2<T, 13>(dst, nfp2, f2, P[13], P[14], a, b, k, wsc2, rng);
-    collide2<T, 15>(dst, nfp2, f2, P[15], P[16], a, b, k, wsc2, rng);
-    collide2<T, 17>(dst, nfp2, f2, P[17], P[18], a, b, k, wsc2, rng);
+    __stcs((unsigned int *)(dst + f2), Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(P[0]), wsc0 * a.Kb),
+                                                    fmaf(k.c1, Half2Bits<T>::hi(P[0]), wsc0 * b.Kb),
+                                                    rng ^ (rng >> 15)));
+    {
+        const Cls wa = make_cls(a, k, wsc1), wb = make_cls(b, k, wsc1);
+        collide2<T, 1>(dst, nfp2, f2, P[1], P[2], a, b, k, wa, wb, rng);
+        collide2<T, 3>(dst, nfp2, f2, P[3], P[4], a, b, k, wa, wb, rng);
+        collide2<T, 5>(dst, nfp2, f2, P[5], P[6], a, b, k, wa, wb, rng);
+    }
+    const Cls wa = make_cls(a, k, wsc2), wb = make_cls(b, k, wsc2);
+    collide2<T, 7>(dst, nfp2, f2, P[7], P[8], a, b, k, wa, wb, rng);
+    collide2<T, 9>(dst, nfp2, f2, P[9], P[10], a, b, k, wa, wb, rng);
+    collide2<T, 11>(dst, nfp2, f2, P[11], P[12], a, b, k, wa, wb, rng);
+    collide2<T, 13>(dst, nfp2, f2, P[13], P[14], a, b, k, wa, wb, rng);
+    collide2<T, 15>(dst, nfp2, f2, P[15], P[16], a, b, k, wa, wb, rng);
+    collide2<T, 17>(dst, nfp2, f2, P[17], P[18], a, b, k, wa, wb, rng);
     if (act & 1u) s.ufield[f] = make_float4(a.ux, a.uy, a.uz, rhoa);
     if (act & 2u) s.ufield[f + 1] = make_float4(b.ux, b.uy, b.uz, rhob);
     if (!(usqa < 0.09f) || !(usqb < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
