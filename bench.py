@@ -378,6 +378,7 @@ def main():
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
     if args.membrane_clusters >= 0:
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
+    fluid_kernel = ("k_fluid", "k_fluid_pair")[int(sim.info()[7])]
     sim.step(max(3, args.warmup))
     sim.sync()
 
@@ -462,7 +463,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"k_fluid<{args.precision}>",
+                         "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"{fluid_kernel}<{args.precision}>",
                          "bytes_per_cell": bpc,
                          "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
             "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "nodes": round(nodes_ms, 5),

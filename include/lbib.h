@@ -302,7 +302,9 @@ LBIB_API lbib_status lbib_fluid_mass(lbib_sim *sim, double *mass);
 LBIB_API lbib_status lbib_fluid_mass_noalloc(lbib_sim *sim, double *mass);
 
 /* Counts (oif_info, Sec. 5).  out[8] = n_templates, n_objects, n_nodes,
- * fluid cells, steps taken, device bytes held, precision, reserved. */
+ * fluid cells, steps taken, device bytes held, precision, and the fluid
+ * kernel the step uses: 0 one cell per thread; 1 two x-adjacent cells per
+ * thread (16-bit storage, even nx, no obstacles, no inlet). */
 LBIB_API lbib_status lbib_info(const lbib_sim *sim, int64_t out[8]);
 
 /* Momentum the nodes would have given to solid corners (Sec. 2 spreading

@@ -1028,7 +1028,7 @@ lbib_status lbib_info(const lbib_sim *s, int64_t out[8]) {
     out[5] = (int64_t)(s->fluid_bytes + s->tpl_bytes + s->node_bytes + s->rep_bytes +
                        (s->solid_mem ? (size_t)s->d.nwords * 4 : 0));
     out[6] = s->p.precision;
-    out[7] = 0;
+    out[7] = fluid_kernel_kind(s->d);
     return LBIB_OK;
 }
 

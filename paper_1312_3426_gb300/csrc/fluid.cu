@@ -36,10 +36,14 @@ __global__ void __launch_bounds__(FLUID_THREADS, 3) k_fluid_pair(SimDev s, int p
     if (f < s.nf) fluid_pair<T>(s, par, f, seed);
 }
 
+static bool pair_shape(const SimDev &s) { return (s.nx & 1) == 0 && !s.solid && !s.in_on; }
+
+int fluid_kernel_kind(const SimDev &s) { return (s.prec != LBIB_POP_F32 && pair_shape(s)) ? 1 : 0; }
+
 template <typename T>
 static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
     if constexpr (sizeof(T) == 2) {
-        if ((s.nx & 1) == 0 && !s.solid && !s.in_on) {
+        if (pair_shape(s)) {
             const int pblocks = (s.nf / 2 + FLUID_THREADS - 1) / FLUID_THREADS;
             k_fluid_pair<T><<<pblocks, FLUID_THREADS, 0, st>>>(s, par, seed);
             return;

@@ -436,33 +436,196 @@ __device__ __forceinline__ uint32_t pull2(const uint16_t *__restrict__ src, uint
            ((uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + 1 + dxp1))) << 16);
 }
 
+// The arithmetic of the two cells runs in packed FP32 instructions (sm_100
+// family: one instruction updates both cells, each component rounded as the
+// scalar instruction would round it); x holds cell f, y cell f+1.
+__device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, v2(-1.0f), a); }  // b * -1 is exact
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// s + E v, E = +-1
+template <int E>
+__device__ __forceinline__ float2 acc2(float2 s, float2 v) {
+    static_assert(E == 1 || E == -1, "unit component");
+    if constexpr (E == 1) return add2(s, v);
+    else return sub2(s, v);
+}
+
+// e_Q . v for a pair representative Q (odd Q: its first non-zero component
+// is +1), with only the non-zero terms.
+template <int Q>
+__device__ __forceinline__ float2 edot2(float2 x, float2 y, float2 z) {
+    constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
+    static_assert(Q % 2 == 1, "pair representative");
+    if constexpr (ex != 0) {
+        static_assert(ex == 1, "leading +1");
+        float2 s = x;
+        if constexpr (ey != 0) s = acc2<ey>(s, y);
+        if constexpr (ez != 0) s = acc2<ez>(s, z);
+        return s;
+    } else if constexpr (ey != 0) {
+        static_assert(ey == 1, "leading +1");
+        if constexpr (ez != 0) return acc2<ez>(y, z);
+        else return y;
+    } else {
+        static_assert(ez == 1, "leading +1");
+        return z;
+    }
+}
+
 template <typename T>
-__device__ __forceinline__ Moments moments_half(const uint32_t (&P)[NQ], bool high) {
-    float h[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) h[q] = high ? Half2Bits<T>::hi(P[q]) : Half2Bits<T>::lo(P[q]);
-    return moments19(h);
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+    return make_float2(Half2Bits<T>::lo(u), Half2Bits<T>::hi(u));
+}
+
+struct Moments2 {
+    float2 r, x, y, z;
+};
+// the difference h_Q - h_{Q+1} of pair Q into the momentum sums
+template <int Q>
+__device__ __forceinline__ void add_diff2(Moments2 &m, float2 d) {
+    if constexpr (d3q19_ex(Q) != 0) m.x = acc2<d3q19_ex(Q)>(m.x, d);
+    if constexpr (d3q19_ey(Q) != 0) m.y = acc2<d3q19_ey(Q)>(m.y, d);
+    if constexpr (d3q19_ez(Q) != 0) m.z = acc2<d3q19_ez(Q)>(m.z, d);
+}
+// The moments of both cells: sum h from the pair sums, sum h e from the
+// pair differences; the axis pairs (1, 3, 5) open the x, y, z sums.
+template <typename T>
+__device__ __forceinline__ Moments2 moments2(const uint32_t (&P)[NQ]) {
+    static_assert(d3q19_ex(1) == 1 && d3q19_ey(3) == 1 && d3q19_ez(5) == 1, "axis pairs 1, 3, 5");
+    Moments2 m;
+    float2 a = unpack2<T>(P[1]), b = unpack2<T>(P[2]);
+    m.r = add2(unpack2<T>(P[0]), add2(a, b));
+    m.x = sub2(a, b);
+    a = unpack2<T>(P[3]), b = unpack2<T>(P[4]);
+    m.r = add2(m.r, add2(a, b));
+    m.y = sub2(a, b);
+    a = unpack2<T>(P[5]), b = unpack2<T>(P[6]);
+    m.r = add2(m.r, add2(a, b));
+    m.z = sub2(a, b);
+#define LBIB_M2(q)                          \
+    a = unpack2<T>(P[q]), b = unpack2<T>(P[q + 1]); \
+    m.r = add2(m.r, add2(a, b));            \
+    add_diff2<q>(m, sub2(a, b));
+    LBIB_M2(7) LBIB_M2(9) LBIB_M2(11) LBIB_M2(13) LBIB_M2(15) LBIB_M2(17)
+#undef LBIB_M2
+    return m;
+}
+
+// Coll, Cls of both cells
+struct Coll2 {
+    float2 ux, uy, uz, Gx, Gy, Gz, Kb, Rb;
+};
+struct Cls2 {
+    float2 K, R, R15, gx, gy, gz;
+};
+
+__device__ __forceinline__ Coll2 make_coll2(const SimDev &s, const CollK &k, const Moments2 &m, float2 Gx, float2 Gy,
+                                            float2 Gz, float2 &rho, float2 &usq) {
+    const float2 inv = v2(s.inv_scale), half = v2(0.5f);
+    const float2 drho = mul2(m.r, inv);
+    rho = add2(drho, v2(s.rho0));
+    // rho is near 1: the fast reciprocal is within 2 ulp
+    const float2 irho = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+    Coll2 c;
+    c.ux = mul2(fma2(half, Gx, mul2(m.x, inv)), irho);
+    c.uy = mul2(fma2(half, Gy, mul2(m.y, inv)), irho);
+    c.uz = mul2(fma2(half, Gz, mul2(m.z, inv)), irho);
+    c.Gx = Gx;
+    c.Gy = Gy;
+    c.Gz = Gz;
+    usq = fma2(c.uz, c.uz, fma2(c.uy, c.uy, mul2(c.ux, c.ux)));
+    const float2 uG = fma2(c.uz, Gz, fma2(c.uy, Gy, mul2(c.ux, Gx)));
+    const float2 K = fma2(mul2(v2(-1.5f), rho), usq, drho);
+    c.Kb = fma2(v2(k.om), K, mul2(v2(-k.fp3), uG));
+    c.Rb = mul2(v2(k.om3), rho);
+    return c;
+}
+
+__device__ __forceinline__ Cls2 make_cls2(const Coll2 &c, const CollK &k, float wsc) {
+    const float2 g = v2(k.fp3 * wsc), w = v2(wsc);
+    const float2 R = mul2(w, c.Rb);
+    return Cls2{mul2(w, c.Kb), R, mul2(v2(1.5f), R), mul2(g, c.Gx), mul2(g, c.Gy), mul2(g, c.Gz)};
+}
+
+// pair_terms for both cells
+template <int Q>
+__device__ __forceinline__ void pair_terms2(const Coll2 &c, const Cls2 &w, float2 &ApB, float2 &AmB) {
+    const float2 eu = edot2<Q>(c.ux, c.uy, c.uz);
+    const float2 eg = edot2<Q>(w.gx, w.gy, w.gz);
+    const float2 B = fma2(w.R, eu, eg);
+    const float2 A = fma2(eu, fma2(w.R15, eu, mul2(v2(3.0f), eg)), w.K);
+    ApB = add2(A, B);
+    AmB = sub2(A, B);
 }
 
 template <typename T, int Q>
 __device__ __forceinline__ void collide2(uint32_t *__restrict__ dst, uint32_t nfp2, uint32_t f2, uint32_t Pq,
-                                         uint32_t Po, const Coll &a, const Coll &b, const CollK &k, const Cls &wa,
-                                         const Cls &wb, uint32_t &rng) {
-    const float2 ta = pair_terms<Q>(a, wa), tb = pair_terms<Q>(b, wb);
+                                         uint32_t Po, const Coll2 &c, const CollK &k, const Cls2 &w,
+                                         uint32_t &rng) {
+    float2 ApB, AmB;
+    pair_terms2<Q>(c, w, ApB, AmB);
+    const float2 oq = fma2(v2(k.c1), unpack2<T>(Pq), ApB), oo = fma2(v2(k.c1), unpack2<T>(Po), AmB);
     rng = rng * 747796405u + 2891336453u;
     const uint32_t r1 = rng ^ (rng >> 15);
     rng = rng * 747796405u + 2891336453u;
     const uint32_t r2 = rng ^ (rng >> 15);
-    __stcs((unsigned int *)(dst + (uint32_t)Q * nfp2 + f2),
-           Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(Pq), ta.x), fmaf(k.c1, Half2Bits<T>::hi(Pq), tb.x), r1));
-    __stcs((unsigned int *)(dst + (uint32_t)(Q + 1) * nfp2 + f2),
-           Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(Po), ta.y), fmaf(k.c1, Half2Bits<T>::hi(Po), tb.y), r2));
+    __stcs((unsigned int *)(dst + (uint32_t)Q * nfp2 + f2), Pack2<T>::rs(oq.x, oq.y, r1));
+    __stcs((unsigned int *)(dst + (uint32_t)(Q + 1) * nfp2 + f2), Pack2<T>::rs(oo.x, oo.y, r2));
+}
+
+// Collision and store of the cell pair (f, f+1) from its pulled populations
+// P (packed pairs, low half: cell f).
+template <typename T>
+__device__ __forceinline__ void pair_update(const SimDev &s, int par, uint32_t f, const uint32_t (&P)[NQ],
+                                            uint32_t step_seed) {
+    uint32_t *__restrict__ dst = (uint32_t *)s.pop[par ^ 1];
+    const uint32_t nfp = (uint32_t)s.nfp;
+    const uint32_t act = (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u;
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+    if (act & 1u) {  // spread force of this step; clear the buffer of the next
+        ga = __ldcg(s.G[par] + f);
+        s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (act & 2u) {
+        gb = __ldcg(s.G[par] + f + 1);
+        s.G[par ^ 1][f + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const CollK k = make_collk(s);
+    float2 rho, usq;
+    const Moments2 m = moments2<T>(P);
+    const Coll2 c = make_coll2(s, k, m, make_float2(s.gx + ga.x, s.gx + gb.x), make_float2(s.gy + ga.y, s.gy + gb.y),
+                               make_float2(s.gz + ga.z, s.gz + gb.z), rho, usq);
+    const float sc = s.scale;
+    const float wsc0 = (float)d3q19_w(0) * sc, wsc1 = (float)d3q19_w(1) * sc, wsc2 = (float)d3q19_w(7) * sc;
+    const uint32_t nfp2 = nfp / 2, f2 = f / 2;
+    uint32_t rng = mix32(f ^ step_seed);
+    rng = rng * 747796405u + 2891336453u;
+    const float2 o0 = fma2(v2(k.c1), unpack2<T>(P[0]), mul2(v2(wsc0), c.Kb));
+    __stcs((unsigned int *)(dst + f2), Pack2<T>::rs(o0.x, o0.y, rng ^ (rng >> 15)));
+    {
+        const Cls2 w = make_cls2(c, k, wsc1);
+        collide2<T, 1>(dst, nfp2, f2, P[1], P[2], c, k, w, rng);
+        collide2<T, 3>(dst, nfp2, f2, P[3], P[4], c, k, w, rng);
+        collide2<T, 5>(dst, nfp2, f2, P[5], P[6], c, k, w, rng);
+    }
+    const Cls2 w = make_cls2(c, k, wsc2);
+    collide2<T, 7>(dst, nfp2, f2, P[7], P[8], c, k, w, rng);
+    collide2<T, 9>(dst, nfp2, f2, P[9], P[10], c, k, w, rng);
+    collide2<T, 11>(dst, nfp2, f2, P[11], P[12], c, k, w, rng);
+    collide2<T, 13>(dst, nfp2, f2, P[13], P[14], c, k, w, rng);
+    collide2<T, 15>(dst, nfp2, f2, P[15], P[16], c, k, w, rng);
+    collide2<T, 17>(dst, nfp2, f2, P[17], P[18], c, k, w, rng);
+    if (act & 1u) s.ufield[f] = make_float4(c.ux.x, c.uy.x, c.uz.x, rho.x);
+    if (act & 2u) s.ufield[f + 1] = make_float4(c.ux.y, c.uy.y, c.uz.y, rho.y);
+    if (!(usq.x < 0.09f) || !(usq.y < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
 }
 
 template <typename T>
 __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uint32_t step_seed) {
     const uint16_t *__restrict__ src = (const uint16_t *)s.pop[par];
-    uint32_t *__restrict__ dst = (uint32_t *)s.pop[par ^ 1];
     const uint32_t nfp = (uint32_t)s.nfp, f = (uint32_t)fi;
     const uint32_t r = s.div_nx.div(f);
     const uint32_t x = f - r * (uint32_t)s.nx;
@@ -477,47 +640,7 @@ __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uin
     LBIB_PULL2(7) LBIB_PULL2(8) LBIB_PULL2(9) LBIB_PULL2(10) LBIB_PULL2(11) LBIB_PULL2(12) LBIB_PULL2(13)
     LBIB_PULL2(14) LBIB_PULL2(15) LBIB_PULL2(16) LBIB_PULL2(17) LBIB_PULL2(18)
 #undef LBIB_PULL2
-
-    const uint32_t act = (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u;
-    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
-    if (act & 1u) {  // spread force of this step; clear the buffer of the next
-        ga = __ldcg(s.G[par] + f);
-        s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    if (act & 2u) {
-        gb = __ldcg(s.G[par] + f + 1);
-        s.G[par ^ 1][f + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const CollK k = make_collk(s);
-    float rhoa, rhob, usqa, usqb;
-    const Moments ma = moments_half<T>(P, false);
-    const Coll a = make_coll(s, k, ma.r, ma.x, ma.y, ma.z, s.gx + ga.x, s.gy + ga.y, s.gz + ga.z, rhoa, usqa);
-    const Moments mb = moments_half<T>(P, true);
-    const Coll b = make_coll(s, k, mb.r, mb.x, mb.y, mb.z, s.gx + gb.x, s.gy + gb.y, s.gz + gb.z, rhob, usqb);
-    const float sc = s.scale;
-    const float wsc0 = (float)d3q19_w(0) * sc, wsc1 = (float)d3q19_w(1) * sc, wsc2 = (float)d3q19_w(7) * sc;
-    const uint32_t nfp2 = nfp / 2, f2 = f / 2;
-    uint32_t rng = mix32(f ^ step_seed);
-    rng = rng * 747796405u + 2891336453u;
-    __stcs((unsigned int *)(dst + f2), Pack2<T>::rs(fmaf(k.c1, Half2Bits<T>::lo(P[0]), wsc0 * a.Kb),
-                                                    fmaf(k.c1, Half2Bits<T>::hi(P[0]), wsc0 * b.Kb),
-                                                    rng ^ (rng >> 15)));
-    {
-        const Cls wa = make_cls(a, k, wsc1), wb = make_cls(b, k, wsc1);
-        collide2<T, 1>(dst, nfp2, f2, P[1], P[2], a, b, k, wa, wb, rng);
-        collide2<T, 3>(dst, nfp2, f2, P[3], P[4], a, b, k, wa, wb, rng);
-        collide2<T, 5>(dst, nfp2, f2, P[5], P[6], a, b, k, wa, wb, rng);
-    }
-    const Cls wa = make_cls(a, k, wsc2), wb = make_cls(b, k, wsc2);
-    collide2<T, 7>(dst, nfp2, f2, P[7], P[8], a, b, k, wa, wb, rng);
-    collide2<T, 9>(dst, nfp2, f2, P[9], P[10], a, b, k, wa, wb, rng);
-    collide2<T, 11>(dst, nfp2, f2, P[11], P[12], a, b, k, wa, wb, rng);
-    collide2<T, 13>(dst, nfp2, f2, P[13], P[14], a, b, k, wa, wb, rng);
-    collide2<T, 15>(dst, nfp2, f2, P[15], P[16], a, b, k, wa, wb, rng);
-    collide2<T, 17>(dst, nfp2, f2, P[17], P[18], a, b, k, wa, wb, rng);
-    if (act & 1u) s.ufield[f] = make_float4(a.ux, a.uy, a.uz, rhoa);
-    if (act & 2u) s.ufield[f + 1] = make_float4(b.ux, b.uy, b.uz, rhob);
-    if (!(usqa < 0.09f) || !(usqb < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
+    pair_update<T>(s, par, f, P, step_seed);
 }
 
 // Seed of the rounding bits of step t.

@@ -188,6 +188,7 @@ struct SmemAttr {
 
 // ---- launchers (fluid.cu) -------------------------------------------------
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);
+int fluid_kernel_kind(const SimDev &s);  // the kernel launch_fluid picks (lbib_info out[7])
 cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
                           cudaStream_t st);
 cudaError_t launch_read_coupling(const SimDev &s, int gpar, float *g_full, cudaStream_t st);

@@ -366,8 +366,34 @@ def test_half_storage_two_cells_per_thread(prec, bound, walls):
     sc = _two_object_scene(walls, nx=38, ny=19, nz=29)
     assert sc.nx % 2 == 0 and (sc.n_fluid_cells // 2) % 256 != 0
     o, g = run_pair(sc, 300, precision=prec, pop_scale_log2=12)
+    assert int(g.info()[7]) == 1
     assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
     assert nodes_maxabs(g, o, 2) <= 1e-3
+
+
+@pytest.mark.parametrize("prec,bound", [("f16s", 5e-3), ("bf16s", 5e-2)])
+@pytest.mark.parametrize("nx,ny,nz,walls,objects,steps", [
+    (32, 19, 29, True, True, 300),
+    (64, 19, 29, False, True, 300),    # periodic y
+    (8, 12, 7, True, False, 400),      # 4 pairs per row
+    (2, 9, 6, False, False, 400),      # one pair per row: both x wraps in every pair
+    (512, 6, 5, True, False, 300),
+    (46, 11, 170, True, False, 200),
+])
+def test_half_storage_two_cells_per_thread_shapes(prec, bound, nx, ny, nz, walls, objects, steps):
+    """The two-cells-per-thread kernel over row widths from one pair to 256
+    pairs: wall rows and the periodic wraps in x, y and z against the
+    oracle, and the total mass."""
+    if objects:
+        sc = _two_object_scene(walls, nx=nx, ny=ny, nz=nz)
+    else:
+        sc = scenes.Scene("rows", nx, ny, nz, walls=walls, tau=0.8, body_force=(2e-5, 0.0, 1e-5), steps=steps)
+    o, g = run_pair(sc, steps, precision=prec, pop_scale_log2=12)
+    assert int(g.info()[7]) == 1
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+    if objects:
+        assert nodes_maxabs(g, o, 2) <= 1e-3
+    assert abs(g.mass() - o.fluid_totals()[0]) <= 1e-5 * o.fluid_totals()[0]
 
 
 # ------------------------------------------------------------- batching
