@@ -156,12 +156,24 @@ __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corne
     lattice_coord(x, ix, wx);
     lattice_coord(y, iy, wy);
     lattice_coord(z, iz, wz);
-    const int cx0 = wrapi(ix, s.nx), cx1 = wrapi(ix + 1, s.nx);
-    const int cz0 = wrapi(iz, s.nz), cz1 = wrapi(iz + 1, s.nz);
+    // one modulo per axis (positions are not wrapped), then the +1 neighbour
+    const int cx0 = wrapi(ix, s.nx), cx1 = cx0 + 1 == s.nx ? 0 : cx0 + 1;
+    const int cz0 = wrapi(iz, s.nz), cz1 = cz0 + 1 == s.nz ? 0 : cz0 + 1;
+    int cy0, cy1;
+    bool in0 = true, in1 = true;
+    if (s.walls) {  // fluid row = lattice row - 1; rows 0 and ny - 1 are solid
+        cy0 = iy - 1;
+        cy1 = iy;
+        in0 = iy >= 1 && iy <= s.ny - 2;
+        in1 = iy >= 0 && iy <= s.ny - 3;
+    } else {
+        cy0 = wrapi(iy, s.ny);
+        cy1 = cy0 + 1 == s.ny ? 0 : cy0 + 1;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-        c.f[k] = fluid_index(s, dx ? cx1 : cx0, iy + dy, dz ? cz1 : cz0);
+        c.f[k] = ((dy ? in1 : in0)) ? (dx ? cx1 : cx0) + s.nx * ((dy ? cy1 : cy0) + s.nyf * (dz ? cz1 : cz0)) : -1;
         if (s.solid && c.f[k] >= 0 && solid_bit(s, c.f[k])) c.f[k] = -1;  // obstacle corner
         c.w[k] = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
     }
@@ -231,8 +243,9 @@ __device__ __forceinline__ void edge_force(const TplDev &T, const Stage &P, int 
     const float lam = L * iL0;
     float kap = 1.f;
     if (T.nonlinear) {  // (lambda^0.5 + lambda^-2.5) / (lambda + lambda^-3)
-        const float sl = sqrtf(lam), il3 = 1.f / (lam * lam * lam);
-        kap = (sl + il3 * sl) / (lam + il3);
+        // lambda stays near 1: the fast reciprocal and quotient are within 2 ulp
+        const float sl = sqrtf(lam), il3 = __fdividef(1.f, lam * lam * lam);
+        kap = __fdividef(sl + il3 * sl, lam + il3);
     }
     const f3 f = (T.ks * kap * (L - L0) * iL0 * il) * d;
     F.add(r.x, f);
@@ -271,8 +284,9 @@ __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, 
     const f3 G = (1.f / 3.f) * (B + C);  // centroid relative to a
     const f3 fv = (T.kv * dV * S * inl * (1.f / 3.f)) * N;  // volume, a third per vertex
     const f3 wa = -1.f * G, wb = B - G, wc = C - G;
+    const float iS = 2.f * inl;  // 1/S
     if (!T.kal_altitude) {
-        const float cw = -T.kal * (S - S0) / S - T.kag * dSg;  // local + global area
+        const float cw = -T.kal * (S - S0) * iS - T.kag * dSg;  // local + global area
         F.add(tr.x, (cw * rsqrtf(dot(wa, wa))) * wa + fv);
         F.add(tr.y, (cw * rsqrtf(dot(wb, wb))) * wb + fv);
         F.add(tr.z, (cw * rsqrtf(dot(wc, wc))) * wc + fv);
@@ -280,7 +294,7 @@ __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, 
     }
     // local area along each vertex's altitude (from the foot on the opposite
     // edge to the vertex), global area along centroid -> vertex
-    const float cl = -T.kal * (S - S0) / S, cg = -T.kag * dSg;
+    const float cl = -T.kal * (S - S0) * iS, cg = -T.kag * dSg;
     const f3 Z = mk(0.f, 0.f, 0.f);
     auto alt = [](f3 p, f3 q, f3 r) {  // component of p - q orthogonal to r - q
         const f3 e = r - q, d = p - q;
