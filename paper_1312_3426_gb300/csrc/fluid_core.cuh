@@ -414,29 +414,30 @@ struct Half2Bits<__nv_bfloat16> {
 
 // The pair of direction Q arriving at cells f, f+1 (low half: cell f).
 // dxm0: x-1 offset of cell f (wraps at x = 0); dxp1: x+1 offset of cell f+1
-// (wraps at x+1 = nx-1).  Every population is read once per step, so the
-// loads are marked streaming (evict first): the velocity and force fields
-// the node update reads next stay in L2 (node update 20.7 -> 18.2 us at
-// 256x128x128; the FP32 kernel ran 6% slower with the same marking).
+// (wraps at x+1 = nx-1).  Marking these loads evict-first in L2 kept the
+// velocity and force fields for the node update that follows (20.7 -> 18.2
+// us at 256x128x128) but slowed the kernel 6% at 512x256x256, where the
+// x-shifted lines shared by neighbouring warps were evicted in between; the
+// loads keep the default policy.
 template <int Q>
 __device__ __forceinline__ uint32_t pull2(const uint16_t *__restrict__ src, uint32_t nfp, uint32_t f, const Nbr &n,
                                           int dxm0, int dxp1) {
     constexpr int ex = d3q19_ex(Q), ey = d3q19_ey(Q), ez = d3q19_ez(Q);
     if ((ey == 1 && n.ylo_solid) || (ey == -1 && n.yhi_solid))
-        return __ldcs((const unsigned int *)(src + (uint32_t)d3q19_opp(Q) * nfp + f));
+        return __ldg((const unsigned int *)(src + (uint32_t)d3q19_opp(Q) * nfp + f));
     int g = (int)f;
     if (ey == 1) g += n.dym;
     if (ey == -1) g += n.dyp;
     if (ez == 1) g += n.dzm;
     if (ez == -1) g += n.dzp;
     const uint16_t *p = src + (uint32_t)Q * nfp;
-    if (ex == 0) return __ldcs((const unsigned int *)(p + (uint32_t)g));  // g even
+    if (ex == 0) return __ldg((const unsigned int *)(p + (uint32_t)g));  // g even
     if (ex == 1)  // cell f from x-1, cell f+1 from x
-        return (uint32_t)__ldcs((const unsigned short *)(p + (uint32_t)(g + dxm0))) |
-               ((uint32_t)__ldcs((const unsigned short *)(p + (uint32_t)g)) << 16);
+        return (uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + dxm0))) |
+               ((uint32_t)__ldg((const unsigned short *)(p + (uint32_t)g)) << 16);
     // ex == -1: cell f from x+1, cell f+1 from x+2 (or the row start)
-    return (uint32_t)__ldcs((const unsigned short *)(p + (uint32_t)(g + 1))) |
-           ((uint32_t)__ldcs((const unsigned short *)(p + (uint32_t)(g + 1 + dxp1))) << 16);
+    return (uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + 1))) |
+           ((uint32_t)__ldg((const unsigned short *)(p + (uint32_t)(g + 1 + dxp1))) << 16);
 }
 
 // The arithmetic of the two cells runs in packed FP32 instructions (sm_100

@@ -14,8 +14,8 @@ Bars: FP16-shifted 1e-3 (the bar the 16-bit form is held to), BF16-shifted
 and the per-step forcing increment of a population is about 1e-6 against
 values near 0.03, so round-to-nearest in FP32 arithmetic makes nearly the
 same error in a cell every step and it accumulates; the measured error is a
-mean bias (+2.3e-4 at 20,000 steps, against +6e-6 for the 40x20x20 channel
-at 1000 steps), while the FP16/BF16 stores round stochastically.
+mean bias (4.3e-4 at 20,000 steps, against about 6e-6 for the 40x20x20
+channel at 1000 steps), while the FP16/BF16 stores round stochastically.
 """
 import numpy as np
 import pytest
