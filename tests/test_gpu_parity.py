@@ -417,6 +417,36 @@ def test_batch_step_equals_individual_steps():
             assert np.abs(xa - xm).max() <= 1e-6
 
 
+def _large_object_scene():
+    """A level-4 sphere (2562 nodes) beside a level-2 one: the batch's
+    membrane launch sizes its shared memory for the largest template."""
+    s = scenes.Scene("large", 36, 26, 30, walls=True, tau=0.9, body_force=(2e-5, 0.0, 0.0), steps=60)
+    n4, t4 = mesh.icosphere(4)
+    n2, t2 = mesh.icosphere(2)
+    s.templates.append(scenes.Template(n4, t4, (8.0, 8.0, 8.0), ks=0.05, kb=0.01, kal=0.1, kag=0.3, kv=0.8))
+    s.templates.append(scenes.Template(n2, t2, (3.0, 3.0, 3.0), ks=0.1, kb=0.03, kal=0.1, kag=0.4, kv=1.0))
+    s.objects.append(scenes.Obj(0, (12.5, 13.0, 15.0), (0.2, 0.1, 0.3)))
+    s.objects.append(scenes.Obj(1, (29.0, 12.0, 8.0), (0.0, 0.5, 0.0)))
+    return s
+
+
+def test_batch_with_large_objects_equals_individual_steps():
+    """Level-4 and level-2 objects in one batch against the same
+    simulations stepped alone."""
+    scs = [_large_object_scene(), _two_object_scene(True, nx=37, ny=19, nz=29)]
+    alone = [lbib.Sim.from_scene(s) for s in scs]
+    mixed = [lbib.Sim.from_scene(s) for s in scs]
+    for a in alone:
+        a.step(60)
+    lbib.lbib_batch_step([m.h for m in mixed], 60)
+    for s, a, m in zip(scs, alone, mixed):
+        ua, um = a.velocity(), m.velocity()
+        assert np.abs(ua - um).max() <= 1e-5 * max(1e-12, np.abs(ua).max())
+        xa, _ = a.read_nodes(-1)
+        xm, _ = m.read_nodes(-1)
+        assert np.abs(xa - xm).max() <= 1e-6
+
+
 def test_batch_matches_oracle():
     scs = [_two_object_scene(True), scenes.channel_sphere(with_object=True)]
     ors = [oracle.Oracle.from_scene(s) for s in scs]
