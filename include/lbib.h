@@ -269,6 +269,19 @@ LBIB_API lbib_status lbib_object_analyze(lbib_sim *sim, int oid, double out[14])
 LBIB_API lbib_status lbib_objects_set_force(lbib_sim *sim, const double *f, int n_obj);
 LBIB_API lbib_status lbib_objects_analyze(lbib_sim *sim, double *out, int64_t cap);
 
+/* The same analysis without waiting, for host loops that keep the device
+ * busy (the result of step t is read while step t+1 runs).
+ * lbib_objects_analyze_async enqueues the analysis of the state after the
+ * steps enqueued so far, and its copy with the status word into slot `slot`
+ * (0 or 1) of a page-locked buffer the library owns, and returns at once.
+ * lbib_objects_analyze_wait waits for that slot and writes it to out
+ * [n_obj][14] (layout as lbib_object_analyze; cap: capacity in objects),
+ * then reports the status word it carried as lbib_sync does.  A slot must be
+ * waited for before it is enqueued again, and a wait needs an enqueued slot:
+ * LBIB_ERR_STATE otherwise; LBIB_ERR_ARG for a slot other than 0 or 1. */
+LBIB_API lbib_status lbib_objects_analyze_async(lbib_sim *sim, int slot);
+LBIB_API lbib_status lbib_objects_analyze_wait(lbib_sim *sim, int slot, double *out, int64_t cap);
+
 /* Per-phase timing with CUDA events on the streams the kernels run on.
  * While enabled (on != 0), lbib_step records events around each kernel of
  * every on-th step (on = 1: every step; the events themselves add a few

@@ -326,6 +326,7 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     for (int i = 0; i < n; ++i) {
         if (sims[i]->stream != st && cudaStreamSynchronize(sims[i]->stream) != cudaSuccess) return LBIB_ERR_CUDA;
         if (cudaStreamSynchronize(sims[i]->aux) != cudaSuccess) return LBIB_ERR_CUDA;
+        if (cudaStreamSynchronize(sims[i]->side) != cudaSuccess) return LBIB_ERR_CUDA;
     }
     cudaError_t e = cudaSuccess;
     const int cluster = sims[0]->cluster;
@@ -392,6 +393,7 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
             if (s->nn_total > 0) {
                 s->dev_newer = true;
                 s->fel_valid = true;  // the last membrane pass used the final positions
+                s->side_ok = false;   // the batch ran on its own streams
             }
         }
     }

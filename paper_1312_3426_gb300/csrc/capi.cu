@@ -142,6 +142,7 @@ lbib_status sim_download_nodes(lbib_sim *s) {
 }
 
 lbib_status sim_upload(lbib_sim *s) {
+    if (s->tables_dirty || s->host_newer) s->side_ok = false;
     if (s->tables_dirty) {
         if (!s->tpl_dev.empty()) {
             if (s->d_tpl) cudaFree(s->d_tpl);
@@ -199,8 +200,14 @@ lbib_status sim_upload(lbib_sim *s) {
     }
     if (s->fext_dirty && !s->objs.empty()) {
         // asynchronous upload through a page-locked staging buffer; the
-        // buffer is refilled only once the previous upload out of it is done
+        // buffer is refilled only once the previous upload out of it is done.
+        // After a step the copy runs on `side` (after the node update that
+        // read the old forces, beside the fluid kernel) and `stream` waits
+        // for it before the next node update.
         const size_t n = s->fext.size();
+        const bool side = s->side_ok;
+        cudaStream_t ust = side ? s->side : s->stream;
+        if (side) LBIB_CUDA(s, cudaStreamWaitEvent(ust, s->ev_nodes, 0), "object forces");
         LBIB_CUDA(s, cudaEventSynchronize(s->ev_fext), "object forces");
         if (n > s->fext_pinned_cap) {
             if (s->fext_pinned) cudaFreeHost(s->fext_pinned);
@@ -210,9 +217,10 @@ lbib_status sim_upload(lbib_sim *s) {
             s->fext_pinned_cap = n;
         }
         std::memcpy(s->fext_pinned, s->fext.data(), n * sizeof(float));
-        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext_pinned, n * sizeof(float), cudaMemcpyHostToDevice, s->stream),
+        LBIB_CUDA(s, cudaMemcpyAsync(s->d_fext, s->fext_pinned, n * sizeof(float), cudaMemcpyHostToDevice, ust),
                   "object forces");
-        LBIB_CUDA(s, cudaEventRecord(s->ev_fext, s->stream), "object forces");
+        LBIB_CUDA(s, cudaEventRecord(s->ev_fext, ust), "object forces");
+        if (side) LBIB_CUDA(s, cudaStreamWaitEvent(s->stream, s->ev_fext, 0), "object forces");
         s->fext_dirty = false;
     }
     if (s->host_newer) {
@@ -378,6 +386,7 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
     int prio_least = 0, prio_greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->aux, cudaStreamNonBlocking, prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_nodes, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_membrane, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fext, cudaEventDisableTiming);
@@ -387,6 +396,7 @@ lbib_status lbib_create(const lbib_fluid_params *p, void *stream, lbib_sim **out
         if (s->ev_membrane) cudaEventDestroy(s->ev_membrane);
         if (s->ev_fext) cudaEventDestroy(s->ev_fext);
         if (s->aux) cudaStreamDestroy(s->aux);
+        if (s->side) cudaStreamDestroy(s->side);
         cudaFree(s->fluid_mem);
         delete s;
         return LBIB_ERR_CUDA;
@@ -403,11 +413,19 @@ void lbib_destroy(lbib_sim *s) {
         cudaStreamSynchronize(s->aux);
         cudaStreamDestroy(s->aux);
     }
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+    }
     if (s->ev_nodes) cudaEventDestroy(s->ev_nodes);
     if (s->ev_membrane) cudaEventDestroy(s->ev_membrane);
     if (s->ev_fext) cudaEventDestroy(s->ev_fext);
     if (s->fext_pinned) cudaFreeHost(s->fext_pinned);
     if (s->status_pinned) cudaFreeHost(s->status_pinned);
+    for (int k = 0; k < 2; ++k) {
+        if (s->ana_pinned[k]) cudaFreeHost(s->ana_pinned[k]);
+        if (s->ana_ev[k]) cudaEventDestroy(s->ana_ev[k]);
+    }
     for (auto &t : s->tpl_mem) cudaFree(t);
     if (s->d_tpl) cudaFree(s->d_tpl);
     if (s->d_obj) cudaFree(s->d_obj);
@@ -809,6 +827,8 @@ lbib_status lbib_step(lbib_sim *s, int n) {
         s->gmode = par;
     }
     s->prof_now = false;
+    // with overlap, ev_nodes marks the last node update
+    s->side_ok = n > 0 && objects && s->overlap;
     if (!s->overlap) s->fel_valid = false;
     if (n > 0 && s->nn_total > 0) s->dev_newer = true;
     return LBIB_OK;
@@ -1062,6 +1082,62 @@ lbib_status lbib_objects_analyze(lbib_sim *s, double *out, int64_t cap) {
     LBIB_CUDA(s, cudaMemcpyAsync(s->status_pinned, s->d.status, 4, cudaMemcpyDeviceToHost, s->stream), "analyze");
     LBIB_CUDA(s, cudaStreamSynchronize(s->stream), "analyze");
     return apply_status(s, *s->status_pinned);
+}
+
+lbib_status lbib_objects_analyze_async(lbib_sim *s, int slot) {
+    LBIB_GUARD(s);
+    if (slot != 0 && slot != 1) return fail(s, LBIB_ERR_ARG, "slot must be 0 or 1");
+    if (s->ana_pending[slot]) return fail(s, LBIB_ERR_STATE, "slot not waited for");
+    const int nobj = (int)s->objs.size();
+    lbib_status r = sim_upload(s);
+    if (r != LBIB_OK) return r;
+    if (s->ana_cap[slot] < nobj || !s->ana_pinned[slot]) {
+        if (s->ana_pinned[slot]) cudaFreeHost(s->ana_pinned[slot]);
+        s->ana_pinned[slot] = nullptr;
+        s->ana_cap[slot] = 0;
+        const int cap = nobj > 0 ? nobj : 1;
+        LBIB_CUDA(s, cudaMallocHost((void **)&s->ana_pinned[slot], ((size_t)cap * 14 + 1) * sizeof(double)),
+                  "analysis buffer");
+        s->ana_cap[slot] = cap;
+    }
+    if (!s->ana_ev[slot]) LBIB_CUDA(s, cudaEventCreateWithFlags(&s->ana_ev[slot], cudaEventDisableTiming), "event");
+    double *h = s->ana_pinned[slot];
+    // After a step the analysis (it reads node state only) runs on `side`
+    // after the node update, beside the fluid and membrane kernels, and
+    // `stream` waits for it before the next node update moves the nodes; the
+    // status word it carries may then miss a flag the running fluid kernel
+    // is about to set (the next read sees it).
+    const bool side = s->side_ok;
+    cudaStream_t ast = side ? s->side : s->stream;
+    if (side) LBIB_CUDA(s, cudaStreamWaitEvent(ast, s->ev_nodes, 0), "analyze");
+    if (nobj > 0) {
+        LBIB_CUDA(s, launch_analyze(s->d, -1, s->d_analyze, ast), "analyze");
+        LBIB_CUDA(s, cudaMemcpyAsync(h, s->d_analyze, (size_t)nobj * 14 * sizeof(double), cudaMemcpyDeviceToHost,
+                                     ast), "analyze");
+    }
+    // the status word after the objects' records (the slot holds cap records)
+    LBIB_CUDA(s, cudaMemcpyAsync(h + (size_t)s->ana_cap[slot] * 14, s->d.status, 4, cudaMemcpyDeviceToHost, ast),
+              "analyze");
+    LBIB_CUDA(s, cudaEventRecord(s->ana_ev[slot], ast), "analyze");
+    if (side) LBIB_CUDA(s, cudaStreamWaitEvent(s->stream, s->ana_ev[slot], 0), "analyze");
+    s->ana_nobj[slot] = nobj;
+    s->ana_pending[slot] = true;
+    return LBIB_OK;
+}
+
+lbib_status lbib_objects_analyze_wait(lbib_sim *s, int slot, double *out, int64_t cap) {
+    LBIB_GUARD(s);
+    if (slot != 0 && slot != 1) return fail(s, LBIB_ERR_ARG, "slot must be 0 or 1");
+    if (!s->ana_pending[slot]) return fail(s, LBIB_ERR_STATE, "nothing enqueued in this slot");
+    const int nobj = s->ana_nobj[slot];
+    if (nobj > 0 && (!out || cap < nobj)) return fail(s, LBIB_ERR_ARG, "capacity too small");
+    s->ana_pending[slot] = false;
+    LBIB_CUDA(s, cudaEventSynchronize(s->ana_ev[slot]), "analyze");
+    const double *h = s->ana_pinned[slot];
+    if (nobj > 0) std::memcpy(out, h, (size_t)nobj * 14 * sizeof(double));
+    uint32_t st;
+    std::memcpy(&st, h + (size_t)s->ana_cap[slot] * 14, 4);
+    return apply_status(s, st);
 }
 
 lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {

@@ -50,6 +50,13 @@ struct lbib_sim {
     int cluster = 1;             // thread blocks per object in the membrane kernel
     bool fext_dirty = false;
     double *d_analyze = nullptr; // [nobj][14] read-out buffer
+    // asynchronous analysis: two page-locked slots of [nobj][14] doubles
+    // followed by the status word, each with its event
+    double *ana_pinned[2] = {nullptr, nullptr};
+    int ana_cap[2] = {0, 0};
+    int ana_nobj[2] = {0, 0};
+    bool ana_pending[2] = {false, false};
+    cudaEvent_t ana_ev[2] = {nullptr, nullptr};
     int d_obj_cap = 0;
 
     // The membrane part of step t+1 runs on a second stream while the fluid
@@ -58,6 +65,12 @@ struct lbib_sim {
     cudaEvent_t ev_nodes = nullptr;     // node update of the current step done
     cudaEvent_t ev_membrane = nullptr;  // membrane forces of the next step ready
     bool fel_valid = false;             // Fel holds the membrane forces of the current node positions
+    // The last step recorded ev_nodes after its node update and nothing has
+    // changed node state or tables since: the per-step object-force upload
+    // and analysis may run on `side` (after ev_nodes) beside the fluid and
+    // membrane kernels
+    bool side_ok = false;
+    cudaStream_t side = nullptr;
     bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
     int membrane_threads = 192;         // block size of the membrane kernel

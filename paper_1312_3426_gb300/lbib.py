@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         "lbib_batch_step": (st, [P, C.c_int, C.c_int]),
         "lbib_objects_set_force": (st, [P, P, C.c_int]),
         "lbib_objects_analyze": (st, [P, P, C.c_int64]),
+        "lbib_objects_analyze_async": (st, [P, C.c_int]),
+        "lbib_objects_analyze_wait": (st, [P, C.c_int, P, C.c_int64]),
         "lbib_profile_enable": (st, [P, C.c_int]),
         "lbib_set_tuning": (st, [P, C.c_int, C.c_int]),
         "lbib_get_tuning": (st, [P, C.c_int, C.POINTER(C.c_int)]),
@@ -286,6 +288,16 @@ def lbib_objects_set_force(h, f):
 def lbib_objects_analyze(h, n_obj, out=None):
     out = out if out is not None else np.zeros((n_obj, 14))
     _check(h, _lib.lbib_objects_analyze(h, _p(out), int(n_obj)))
+    return out
+
+
+def lbib_objects_analyze_async(h, slot):
+    _check(h, _lib.lbib_objects_analyze_async(h, int(slot)))
+
+
+def lbib_objects_analyze_wait(h, slot, n_obj, out=None):
+    out = out if out is not None else np.zeros((max(n_obj, 1), 14))
+    _check(h, _lib.lbib_objects_analyze_wait(h, int(slot), _p(out), int(n_obj)))
     return out
 
 

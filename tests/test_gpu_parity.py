@@ -302,6 +302,41 @@ def test_analyze_matches_oracle():
         assert np.abs(a[11:14] - V.mean(0)).max() < 1e-8
 
 
+def test_async_analysis_equals_the_waiting_form():
+    """Two slots in flight: step k's analysis read after step k+1 was
+    enqueued equals the waiting form run at the same step; the slot rules."""
+    sc = _two_object_scene(True)
+    g = lbib.Sim.from_scene(sc)
+    h = lbib.Sim.from_scene(sc)
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.lbib_objects_analyze_wait(g.h, 0, 2)
+    assert e.value.status == -8
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.lbib_objects_analyze_async(g.h, 2)
+    assert e.value.status == -1
+    got = []
+    forces = [np.array([[1e-4 * (k + 1), 0.0, -5e-5 * k], [0.0, 2e-5 * k, 0.0]]) for k in range(6)]
+    for k in range(6):
+        # after a step the force upload and the analysis run beside the fluid
+        # kernel on the second stream
+        lbib.lbib_objects_set_force(g.h, forces[k])
+        g.step(5)
+        lbib.lbib_objects_analyze_async(g.h, k & 1)
+        if k == 0:
+            with pytest.raises(lbib.LbibError) as e:  # slot 0 not waited for
+                lbib.lbib_objects_analyze_async(g.h, 0)
+            assert e.value.status == -8
+        if k > 0:
+            got.append(lbib.lbib_objects_analyze_wait(g.h, (k - 1) & 1, 2).copy())
+    got.append(lbib.lbib_objects_analyze_wait(g.h, 5 & 1, 2).copy())
+    for k in range(6):
+        lbib.lbib_objects_set_force(h.h, forces[k])
+        h.step(5)
+        # a second run of the same steps differs only by the order of the
+        # floating-point atomics of the spreading
+        assert np.allclose(h.objects_analyze(), got[k], rtol=1e-6, atol=1e-9), k
+
+
 def test_template_topology_equals_mesh_check():
     sc = _two_object_scene(True)
     g = lbib.Sim.from_scene(sc)
