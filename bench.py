@@ -121,10 +121,15 @@ def measured_peak():
 
 
 def kernel_source_hash():
+    """Hash of the fluid kernel sources without their comments and blank
+    lines (a comment edit does not change what was profiled)."""
     h = hashlib.sha256()
     for rel in ("paper_1312_3426_gb300/csrc/fluid_core.cuh", "paper_1312_3426_gb300/csrc/fluid.cu"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -11,9 +11,10 @@
 namespace lbib {
 
 // Storage of one population.  FP32 is stored as is.  FP16/BF16 store the
-// deviation times 2^s with stochastic rounding: the conversion rounds up
-// with probability equal to the dropped fraction of a unit in the last
-// place, so the stored value is unbiased.  Rounding to nearest would turn
+// deviation times 2^s with stochastic rounding: the conversion moves to the
+// neighbouring representable value of larger magnitude with probability
+// equal to the dropped fraction of a unit in the last place, so the stored
+// value is unbiased.  Rounding to nearest would turn
 // the per-step forcing increment, which is far below one unit in the last
 // place of a 16-bit number once the flow has built up, into a systematic
 // error.  The rounding is the hardware's (cvt.rs, which converts two FP32
@@ -167,8 +168,8 @@ __device__ __forceinline__ float pull(const SimDev &s, const T *__restrict__ src
 //   w 2^s B = Rc (e.u) + e.Gc,   w 2^s A = Kc + (e.u) (R15 (e.u) + 3 e.Gc).
 // A does not reuse the rounded B (A = Kc + 1.5 (e.u) (B + e.Gc) is the same
 // number in exact arithmetic): that product of e.u with a rounded multiple
-// of e.u has a rounding error of one sign, which drifted the total mass by
-// about 1e-9 per cell and step with 16-bit storage.
+// of e.u has a rounding error of one sign, which drifted the total mass of
+// a 512x256x256 channel with 16-bit storage by 7.6e-6 in 20,000 steps.
 struct Coll {
     float ux, uy, uz, Gx, Gy, Gz, Kb, Rb;
 };
