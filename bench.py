@@ -367,7 +367,9 @@ def main():
                              "kernel": "whole batched step (all kernels)", "bytes_per_cell": bpc,
                              "peak_source": peak_kind + " copy bandwidth"},
                 "nodes_per_s": round(world * nodes * args.steps / (ms / 1e3), 1),
-                "gpu_launches": args.steps * 3 + args.steps // 16,
+                # per step: fluid, node and membrane launches; the counter
+                # advance per 16-step graph; one mask-rebuild launch per 128
+                "gpu_launches": args.steps * 3 + args.steps // 16 + args.steps // 128,
                 "clocks": clocks, "e2e": None, "cpu_baseline": None,
             }
             print(json.dumps(line), flush=True)

@@ -204,6 +204,16 @@ __device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
     return c;
 }
 
+// Marks the cells around node i (global index) as active; a node that is
+// not finite (a failed simulation) marks nothing.
+__device__ __forceinline__ void mark_node(const SimDev &s, int i) {
+    const int NN = s.nn_total;
+    const df x{s.Xh[i], s.Xl[i]}, y{s.Xh[NN + i], s.Xl[NN + i]}, z{s.Xh[2 * NN + i], s.Xl[2 * NN + i]};
+    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) return;
+    const int3 c = lower_corner(x, y, z);
+    mark_halo(s, c.x, c.y, c.z);
+}
+
 namespace cg = cooperative_groups;
 
 // Shared memory per block: per node of the largest template the staged
