@@ -1,0 +1,68 @@
+"""bench.py host logic on CPU: the reference arm (the FP64 oracle on the
+host cores) prints one JSON line with the contract's keys, a non-zero rank
+prints nothing, and the profiled-traffic lookup is keyed by the kernel
+source without its comments.  No GPU is touched."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_line():
+    p = _run(["--impl", "reference", "--workload", "sphere40", "--steps", "3", "--warmup", "1"])
+    assert p.returncode == 0, p.stderr
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["higher_is_better"] is True
+    assert d["steps"] == 3 and d["warmup"] == 1 and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert "3 of the 3 requested" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    p = _run(["--impl", "reference", "--workload", "sphere40", "--steps", "1", "--warmup", "1"], {"RANK": "1"})
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
+
+
+def test_traffic_lookup_ignores_comments(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_1312_3426_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    code = "int f(int x) {\n    return x + 1;\n}\n"
+    (csrc / "fluid_core.cuh").write_text("// header\n" + code)
+    (csrc / "fluid.cu").write_text(code)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    (csrc / "fluid_core.cuh").write_text("// another header\n\n" + code.replace("+ 1;", "+ 1;  // add one"))
+    assert bench.kernel_source_hash() == h0
+    (csrc / "fluid.cu").write_text(code.replace("+ 1", "+ 2"))
+    assert bench.kernel_source_hash() != h0
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h1 = bench.kernel_source_hash()
+    (prof / "k_fluid_dram_traffic.md").write_text(
+        f"traffic: workload=rbc256 precision=f32 source_hash={h1} dram_bytes_per_cell=150.0\n"
+        f"traffic: workload=rbc256 precision=f16s source_hash={h0} dram_bytes_per_cell=75.0\n")
+    assert bench.profiled_traffic("rbc256", "f32", 10) == 1500
+    assert bench.profiled_traffic("rbc256", "f16s", 10) is None   # taken on other code
+    assert bench.profiled_traffic("rbc512", "f32", 10) is None
