@@ -368,8 +368,10 @@ def main():
                              "peak_source": peak_kind + " copy bandwidth"},
                 "nodes_per_s": round(world * nodes * args.steps / (ms / 1e3), 1),
                 # per step: fluid, node and membrane launches; the counter
-                # advance per 16-step graph; one mask-rebuild launch per 128
-                "gpu_launches": args.steps * 3 + args.steps // 16 + args.steps // 128,
+                # advance per 16-step graph; every 128 steps one mask-rebuild
+                # launch per channel with cells
+                "gpu_launches": args.steps * 3 + args.steps // 16
+                + (args.steps // 128) * sum(1 for x in scs if x.objects),
                 "clocks": clocks, "e2e": None, "cpu_baseline": None,
             }
             print(json.dumps(line), flush=True)

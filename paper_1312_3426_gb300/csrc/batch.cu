@@ -70,17 +70,6 @@ __global__ void __launch_bounds__(IB_THREADS, 3)
     if (i < s.nn_total) node_step(s, i, (int)((t_base[it.x] + step_off) & 1));
 }
 
-// Active-cell marks of the flagged simulations (their masks were cleared):
-// one launch over the node items instead of one per simulation.
-__global__ void __launch_bounds__(IB_THREADS)
-    k_batch_mark(const SimDev *__restrict__ sims, const int *__restrict__ flags, const int2 *__restrict__ items) {
-    const int2 it = items[blockIdx.x];  // (simulation, first node)
-    if (!flags[it.x]) return;
-    const SimDev &s = sims[it.x];
-    const int i = it.y + (int)threadIdx.x;
-    if (i < s.nn_total) mark_node(s, i);
-}
-
 __global__ void __launch_bounds__(IB_THREADS, 4)
     k_batch_membrane(const SimDev *__restrict__ sims, const int2 *__restrict__ items) {
     cg::cluster_group cl = cg::this_cluster();
@@ -104,8 +93,6 @@ struct BatchPlan {
     int cluster = 0, device = -1, mthreads = IB_THREADS;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
-    int *d_flags = nullptr;        // simulations whose active-cell mask is rebuilt
-    std::vector<int> h_flags;
     int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
     int n_flp[8] = {};  // fluid items per kernel variant (see fluid_group)
     int n_fl = 0, n_nd = 0, n_mb = 0;
@@ -124,10 +111,8 @@ struct BatchPlan {
         cudaFree(d_sims);
         cudaFree(d_t);
         cudaFree(d_items);
-        cudaFree(d_flags);
         d_sims = nullptr;
         d_t = nullptr;
-        d_flags = nullptr;
         d_items = nullptr;
         sims.clear();
         serial.clear();
@@ -202,7 +187,6 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
     cudaError_t e;
     if ((e = cudaMalloc(&g_plan.d_sims, n * sizeof(SimDev))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&g_plan.d_t, n * sizeof(long long))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&g_plan.d_flags, n * sizeof(int))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&g_plan.d_items, std::max<size_t>(1, items.size()) * sizeof(int2))) != cudaSuccess) return e;
     if (!items.empty() &&
         (e = cudaMemcpyAsync(g_plan.d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, st)) !=
@@ -252,27 +236,6 @@ static cudaError_t launch_membrane_batch(cudaStream_t st) {
                                        (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd));
     // object-object repulsion of the simulations that set it (per simulation)
     return e == cudaSuccess ? launch_repulsion_batch(st) : e;
-}
-
-// Periodic rebuild of the active-cell masks (see sim_remark) of the
-// simulations due for it: their masks cleared, then one marking launch.
-static cudaError_t remark_batch(lbib_sim *const *sims, int n, cudaStream_t st) {
-    g_plan.h_flags.assign(n, 0);
-    bool any = false;
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        if (sims[i]->since_mark < ACTIVE_RESET_STEPS) continue;
-        e = cudaMemsetAsync(sims[i]->d.amask, 0, (size_t)sims[i]->d.nwords * 4, st);
-        g_plan.h_flags[i] = 1;
-        sims[i]->since_mark = 0;
-        any = true;
-    }
-    if (e != cudaSuccess || !any || g_plan.n_nd == 0) return e;
-    // pageable source: staged by the call, so the vector may change after it
-    e = cudaMemcpyAsync(g_plan.d_flags, g_plan.h_flags.data(), n * sizeof(int), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    k_batch_mark<<<g_plan.n_nd, IB_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_flags, g_plan.d_items + g_plan.n_fl);
-    return cudaGetLastError();
 }
 
 // Steps step_off .. step_off + k - 1 relative to the device step counters,
@@ -391,7 +354,8 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
 
     int done = 0;
     while (e == cudaSuccess && done < n_steps) {
-        e = remark_batch(sims, n, st);
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            if (sims[i]->since_mark >= ACTIVE_RESET_STEPS) e = sim_remark(sims[i], st);
         if (e != cudaSuccess) break;
         const int left = n_steps - done;
         const int k = left >= LBIB_BATCH_GRAPH_STEPS ? LBIB_BATCH_GRAPH_STEPS : left;

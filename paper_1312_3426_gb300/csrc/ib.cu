@@ -178,7 +178,12 @@ cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st) {
 // Marks the cells around every node as active (after the mask was cleared).
 __global__ void k_mark_all(SimDev s) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < s.nn_total) mark_node(s, i);
+    if (i >= s.nn_total) return;
+    const int NN = s.nn_total;
+    const df x{s.Xh[i], s.Xl[i]}, y{s.Xh[NN + i], s.Xl[NN + i]}, z{s.Xh[2 * NN + i], s.Xl[2 * NN + i]};
+    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) return;
+    const int3 c = lower_corner(x, y, z);
+    mark_halo(s, c.x, c.y, c.z);
 }
 
 cudaError_t launch_mark_all(const SimDev &s, cudaStream_t st) {

@@ -179,42 +179,18 @@ __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corne
     }
 }
 
+__device__ __forceinline__ void mark(uint32_t *mask, int f) { atomicOr(mask + (f >> 5), 1u << (f & 31)); }
+
 // Marks the 4x4x4 lattice nodes (i0-1 .. i0+2, ...) around lower corner
-// (ix, iy, iz) as active (rows in a wall excepted).  One modulo per axis,
-// then +1 steps with wrap; the up to 4 cells of a row go to their mask
-// words with one atomicOr per word touched.
+// (ix, iy, iz) as active.
 __device__ __forceinline__ void mark_halo(const SimDev &s, int ix, int iy, int iz) {
-    const int cx0 = wrapi(ix - 1, s.nx);
-    int cz = wrapi(iz - 1, s.nz);
-    const int cyw0 = s.walls ? 0 : wrapi(iy - 1, s.ny);
-    for (int dz = 0; dz < 4; ++dz) {
-        int cyw = cyw0;
-        for (int dy = -1; dy <= 2; ++dy) {
-            int cy;  // fluid row of lattice row iy + dy, or none
-            if (s.walls) {
-                const int ly = iy + dy;
-                cy = (ly >= 1 && ly <= s.ny - 2) ? ly - 1 : -1;
-            } else {
-                cy = cyw;
-                cyw = cyw + 1 == s.ny ? 0 : cyw + 1;
+    for (int dz = -1; dz <= 2; ++dz) {
+        const int cz = wrapi(iz + dz, s.nz);
+        for (int dy = -1; dy <= 2; ++dy)
+            for (int dx = -1; dx <= 2; ++dx) {
+                const int f = fluid_index(s, wrapi(ix + dx, s.nx), iy + dy, cz);
+                if (f >= 0) mark(s.amask, f);
             }
-            if (cy < 0) continue;
-            const int row = s.nx * (cy + s.nyf * cz);
-            int cx = cx0, word = -1;
-            uint32_t bits = 0u;
-            for (int dx = 0; dx < 4; ++dx) {
-                const int f = row + cx;
-                if ((f >> 5) != word) {
-                    if (bits) atomicOr(s.amask + word, bits);
-                    word = f >> 5;
-                    bits = 0u;
-                }
-                bits |= 1u << (f & 31);
-                cx = cx + 1 == s.nx ? 0 : cx + 1;
-            }
-            atomicOr(s.amask + word, bits);
-        }
-        cz = cz + 1 == s.nz ? 0 : cz + 1;
     }
 }
 
@@ -226,16 +202,6 @@ __device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
     lattice_coord(y, c.y, w);
     lattice_coord(z, c.z, w);
     return c;
-}
-
-// Marks the cells around node i (global index) as active; a node that is
-// not finite (a failed simulation) marks nothing.
-__device__ __forceinline__ void mark_node(const SimDev &s, int i) {
-    const int NN = s.nn_total;
-    const df x{s.Xh[i], s.Xl[i]}, y{s.Xh[NN + i], s.Xl[NN + i]}, z{s.Xh[2 * NN + i], s.Xl[2 * NN + i]};
-    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) return;
-    const int3 c = lower_corner(x, y, z);
-    mark_halo(s, c.x, c.y, c.z);
 }
 
 namespace cg = cooperative_groups;
