@@ -39,6 +39,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -168,14 +169,19 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-            self.fh = open(self.path, "w")
+            self.fh = tempfile.NamedTemporaryFile("w", prefix="lbib_clocks_", suffix=".csv", delete=False)
+            self.path = self.fh.name
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
             self.proc = None
+            if self.path:
+                self.fh.close()
+                try:
+                    os.unlink(self.path)
+                except OSError:
+                    pass
 
     def stop(self):
         if self.proc is None:
@@ -187,18 +193,23 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                p = [x.strip() for x in line.split(",")]
-                if len(p) < 8:
-                    continue
-                if self.uuid and self.uuid not in p[0] and not p[0].endswith(self.uuid):
-                    continue
-                try:
-                    rows.append((float(p[1]), float(p[2]), p[4:8]))
-                except ValueError:
-                    continue
+            lines = f.readlines()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        rows = []
+        for line in lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            if self.uuid and self.uuid not in p[0] and not p[0].endswith(self.uuid):
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[4:8]))
+            except ValueError:
+                continue
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

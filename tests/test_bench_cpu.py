@@ -66,3 +66,36 @@ def test_traffic_lookup_ignores_comments(tmp_path, monkeypatch):
     assert bench.profiled_traffic("rbc256", "f32", 10) == 1500
     assert bench.profiled_traffic("rbc256", "f16s", 10) is None   # taken on other code
     assert bench.profiled_traffic("rbc512", "f32", 10) is None
+
+
+def test_clock_sampler_with_a_fake_nvidia_smi(tmp_path, monkeypatch):
+    """The sampler's parse of `nvidia-smi --query-gpu` lines: median SM clock,
+    max clock, active throttle reasons, only the GPU asked for; its temporary
+    file is removed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo 'GPU-aaa, 1980, 2070, 900.1, Not Active, Not Active, Not Active, Active'\n"
+                    "echo 'GPU-aaa, 2070, 2070, 910.2, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo 'GPU-aaa, 2070, 2070, 905.0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo 'GPU-bbb, 300, 2070, 100.0, Active, Not Active, Not Active, Not Active'\n"
+                    "echo 'garbage line'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    c = bench.ClockSampler("GPU-aaa")
+    c.start()
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not os.path.exists(c.path)
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    c = bench.ClockSampler(None)
+    c.start()
+    assert c.stop() is None
+    assert c.path is None or not os.path.exists(c.path)
