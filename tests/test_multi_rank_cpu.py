@@ -35,7 +35,7 @@ def _rank(rank, world, port, out):
 def test_replicas_timed_by_slowest_rank_and_summed():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)

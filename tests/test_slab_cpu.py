@@ -82,7 +82,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.parametrize("world", [2, 3])
 def test_slab_decomposition_equals_the_whole_box(world):
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
