@@ -269,8 +269,9 @@ LBIB_API lbib_status lbib_object_analyze(lbib_sim *sim, int oid, double out[14])
 LBIB_API lbib_status lbib_objects_set_force(lbib_sim *sim, const double *f, int n_obj);
 LBIB_API lbib_status lbib_objects_analyze(lbib_sim *sim, double *out, int64_t cap);
 
-/* The same analysis without waiting, for host loops that keep the device
- * busy (the result of step t is read while step t+1 runs).
+/* The same object analysis (Sec. 5) without waiting, for host loops that
+ * keep the device busy (the result of step t is read while step t+1 runs;
+ * the paper's main loop reads object properties every iteration, Sec. 6).
  * lbib_objects_analyze_async enqueues the analysis of the state after the
  * steps enqueued so far, and its copy with the status word into slot `slot`
  * (0 or 1) of a page-locked buffer the library owns, and returns at once.
