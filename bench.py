@@ -234,6 +234,18 @@ def cpu_baseline(sc, target_s):
             "nodes_per_s": round(sc.n_nodes * k / dt, 1)}
 
 
+def e2e_record(nf, steps, dt_s, dt_sync_s, world, nobj):
+    """The `e2e` object: MLUPS of the host loop that reads step k's analysis
+    after enqueueing step k+1, the bytes it moves per step (forces up: 3 FP32
+    per object; analysis down: 14 FP64 per object and the status word), and
+    the MLUPS of the loop that waits for every step."""
+    return {"value": round(whole_job_mlups(nf, steps, dt_s * 1e3, world), 2), "unit": "MLUPS",
+            "h2d_bytes_per_step": 12 * nobj, "d2h_bytes_per_step": 14 * 8 * nobj + 4,
+            "loop": "per step: forces up from pinned memory, step, analysis + status enqueued into a pinned slot; "
+                    "step k's analysis read after step k+1 is enqueued",
+            "synchronous_value": round(whole_job_mlups(nf, steps, dt_sync_s * 1e3, world), 2)}
+
+
 def reference_run(sc, warmup, steps, budget_s=120.0):
     """The FP64 oracle as it stands on the host cores: `warmup` untimed full
     steps (at most 2), then min(steps, as many as fit in budget_s) timed
@@ -478,11 +490,7 @@ def main():
                 sim.sync()
         barrier()
         dt_sync = max_over_ranks(time.perf_counter() - t0, dev)
-        e2e = {"value": round(whole_job_mlups(nf, k_e2e, dt * 1e3, world), 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 12 * nobj,  # 3 FP32 per object "d2h_bytes_per_step": 14 * 8 * nobj + 4,
-               "loop": "per step: forces up from pinned memory, step, analysis + status enqueued into a pinned slot; "
-                       "step k's analysis read after step k+1 is enqueued",
-               "synchronous_value": round(whole_job_mlups(nf, k_e2e, dt_sync * 1e3, world), 2)}
+        e2e = e2e_record(nf, k_e2e, dt, dt_sync, world, nobj)
 
     serving = None
     if world == 1 and not args.no_serving:

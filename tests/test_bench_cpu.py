@@ -99,3 +99,13 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     c.start()
     assert c.stop() is None
     assert c.path is None or not os.path.exists(c.path)
+
+
+def test_e2e_record_keys():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.e2e_record(4_000_000, 100, 0.02, 0.025, 1, 200)
+    assert set(r) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert r["unit"] == "MLUPS" and r["h2d_bytes_per_step"] == 2400 and r["d2h_bytes_per_step"] == 22404
+    assert r["value"] == round(bench.whole_job_mlups(4_000_000, 100, 20.0, 1), 2)
+    assert r["synchronous_value"] < r["value"]
