@@ -136,3 +136,18 @@ def test_poiseuille_profile_tau1_matches_quoted_error():
 def test_channel_is_invariant_along_x_and_z_and_symmetric():
     u, _, _ = _poiseuille(1.0, steps=400)
     assert np.abs(u - u[::-1]).max() < 1e-16
+
+
+def test_density_readout_uniform_in_driven_channel_and_mass_of_the_box():
+    """The steady body-force-driven channel has a uniform pressure, so the
+    density read-out is rho0 in every fluid cell (Eq. lbequation: the force
+    adds no mass); at rest after initialisation it is rho0 too; and the
+    read-out sums to the conserved total over the fluid cells."""
+    o = _box(3, 12, 2, walls=True, tau=0.9, g=(1e-5, 0, 0))
+    rho = o.density()
+    assert np.abs(rho[:, 1:-1, :] - 1.0).max() == 0.0
+    o.step(3000)
+    rho = o.density()[:, 1:-1, :]
+    assert np.abs(rho - 1.0).max() < 1e-12
+    assert abs(rho.sum() - o.fluid_totals()[0]) < 1e-10
+    assert abs(rho.sum() - 3 * 10 * 2) < 1e-10
