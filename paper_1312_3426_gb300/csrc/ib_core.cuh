@@ -43,6 +43,7 @@
 
 #include <cooperative_groups.h>
 
+#include "lattice_index.h"
 #include "lbib_internal.h"
 
 namespace lbib {
@@ -108,74 +109,19 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-__device__ __forceinline__ int wrapi(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
-}
-
-// Fluid index of lattice node (cx, cy, cz) (cx, cz already wrapped), or -1
-// when the node is in a solid row (or outside the walled box).
-__device__ __forceinline__ int fluid_index(const SimDev &s, int cx, int cy, int cz) {
-    if (s.walls) {
-        if (cy < 1 || cy > s.ny - 2) return -1;
-        cy -= 1;
-    } else {
-        cy = wrapi(cy, s.ny);
-    }
-    return cx + s.nx * (cy + s.nyf * cz);
-}
-
 struct Corners {
     int f[8];
     float w[8];
 };
 
-// Lower lattice index and fraction of one coordinate given as hi + lo:
-// i0 = floor(x - 1/2), w = x - 1/2 - i0 in [0, 1).  x.hi - 1/2 and the
-// subtraction of the integer are exact for |x| < 2^22.
-__device__ __forceinline__ void lattice_coord(df x, int &i0, float &w) {
-    const float p = x.hi - 0.5f;
-    float fl = floorf(p);
-    float fr = (p - fl) + x.lo;
-    if (fr < 0.f) {
-        fl -= 1.f;
-        fr += 1.f;
-    } else if (fr >= 1.f) {
-        fl += 1.f;
-        fr -= 1.f;
-    }
-    i0 = (int)fl;
-    w = fr;
-}
-
-// Trilinear weights: corner (i0+dx, j0+dy, k0+dz) gets the volume of the
-// box between the point and the diagonally opposite corner.
+// The 8 interpolation corners of a node (lattice_index.h); a corner on an
+// obstacle cell counts as solid.
 __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corners &c) {
-    int ix, iy, iz;
-    float wx, wy, wz;
-    lattice_coord(x, ix, wx);
-    lattice_coord(y, iy, wy);
-    lattice_coord(z, iz, wz);
-    // one modulo per axis (positions are not wrapped), then the +1 neighbour
-    const int cx0 = wrapi(ix, s.nx), cx1 = cx0 + 1 == s.nx ? 0 : cx0 + 1;
-    const int cz0 = wrapi(iz, s.nz), cz1 = cz0 + 1 == s.nz ? 0 : cz0 + 1;
-    int cy0, cy1;
-    bool in0 = true, in1 = true;
-    if (s.walls) {  // fluid row = lattice row - 1; rows 0 and ny - 1 are solid
-        cy0 = iy - 1;
-        cy1 = iy;
-        in0 = iy >= 1 && iy <= s.ny - 2;
-        in1 = iy >= 0 && iy <= s.ny - 3;
-    } else {
-        cy0 = wrapi(iy, s.ny);
-        cy1 = cy0 + 1 == s.ny ? 0 : cy0 + 1;
-    }
+    corner_cells(s, x.hi, x.lo, y.hi, y.lo, z.hi, z.lo, c.f, c.w);
+    if (s.solid) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-        c.f[k] = ((dy ? in1 : in0)) ? (dx ? cx1 : cx0) + s.nx * ((dy ? cy1 : cy0) + s.nyf * (dz ? cz1 : cz0)) : -1;
-        if (s.solid && c.f[k] >= 0 && solid_bit(s, c.f[k])) c.f[k] = -1;  // obstacle corner
-        c.w[k] = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+        for (int k = 0; k < 8; ++k)
+            if (c.f[k] >= 0 && solid_bit(s, c.f[k])) c.f[k] = -1;
     }
 }
 
@@ -184,23 +130,16 @@ __device__ __forceinline__ void mark(uint32_t *mask, int f) { atomicOr(mask + (f
 // Marks the 4x4x4 lattice nodes (i0-1 .. i0+2, ...) around lower corner
 // (ix, iy, iz) as active.
 __device__ __forceinline__ void mark_halo(const SimDev &s, int ix, int iy, int iz) {
-    for (int dz = -1; dz <= 2; ++dz) {
-        const int cz = wrapi(iz + dz, s.nz);
-        for (int dy = -1; dy <= 2; ++dy)
-            for (int dx = -1; dx <= 2; ++dx) {
-                const int f = fluid_index(s, wrapi(ix + dx, s.nx), iy + dy, cz);
-                if (f >= 0) mark(s.amask, f);
-            }
-    }
+    for_each_halo(s, ix, iy, iz, [&](int f) { mark(s.amask, f); });
 }
 
 // Lower lattice corner of a position.
 __device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
     int3 c;
     float w;
-    lattice_coord(x, c.x, w);
-    lattice_coord(y, c.y, w);
-    lattice_coord(z, c.z, w);
+    lattice_coord(x.hi, x.lo, c.x, w);
+    lattice_coord(y.hi, y.lo, c.y, w);
+    lattice_coord(z.hi, z.lo, c.z, w);
     return c;
 }
 
