@@ -342,6 +342,11 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     bool same_dev = (int)g_plan.dev.size() == n;
     for (int i = 0; i < n && same_dev; ++i) same_dev = std::memcmp(&g_plan.dev[i], &sims[i]->d, sizeof(SimDev)) == 0;
     if (e == cudaSuccess && !same_dev) {
+        // the batched kernels read the descriptors from the device copy, but
+        // the repulsion launches of a captured graph hold them by value: a
+        // changed descriptor (repulsion switched or retuned, node arrays
+        // reallocated) needs a new graph
+        g_plan.release_graph();
         g_plan.dev.resize(n);
         for (int i = 0; i < n; ++i) g_plan.dev[i] = sims[i]->d;
         e = cudaMemcpyAsync(g_plan.d_sims, g_plan.dev.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, st);

@@ -73,11 +73,15 @@ lbib_status lbib_server_advance(lbib_server *srv, int64_t *done, int cap, int *n
         if (r == LBIB_ERR_ARG) return r;
         srv->advances++;
         for (auto &e : srv->res) {
-            if (r != LBIB_OK && lbib_sync(e.sim) != LBIB_OK) {
-                e.left = 0;  // failed (status sticky on the simulation): retire it now
+            if (r != LBIB_OK) {
+                // lbib_batch_step failed: a device error makes every
+                // simulation of the batch sticky, and one that entered the
+                // call sticky or failed to prepare stays so; those are
+                // retired now as failed.  A simulation that lbib_sync still
+                // finds healthy did not advance and runs again next time.
+                if (lbib_sync(e.sim) != LBIB_OK) e.left = 0;
                 continue;
             }
-            if (r != LBIB_OK) continue;  // a healthy simulation did not advance: run it again
             e.left -= k;
             srv->updates += e.cells * k;
         }
