@@ -25,14 +25,19 @@
 namespace lbib {
 
 template <typename T, bool BC>
-__global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed) {
+__global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed, int pf) {
+    prefetch_sources<sizeof(T), FLUID_THREADS>(s, s.pop[par], pf);
     fluid_block<T, BC>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
 // 16-bit storage, even nx, no obstacles, no inlet: two cells per thread.
+// Blocks of 128 threads (6 per SM at 80 registers): when a membrane block
+// shares the SM, one of six fluid blocks gives way instead of one of three.
+constexpr int PAIR_THREADS = 128;
 template <typename T>
-__global__ void __launch_bounds__(FLUID_THREADS, 3) k_fluid_pair(SimDev s, int par, uint32_t seed) {
-    const int f = 2 * (int)(blockIdx.x * FLUID_THREADS + threadIdx.x);
+__global__ void __launch_bounds__(PAIR_THREADS, 6) k_fluid_pair(SimDev s, int par, uint32_t seed, int pf) {
+    prefetch_sources<2, 2 * PAIR_THREADS>(s, s.pop[par], pf);
+    const int f = 2 * (int)(blockIdx.x * PAIR_THREADS + threadIdx.x);
     if (f < s.nf) fluid_pair<T>(s, par, f, seed);
 }
 
@@ -40,19 +45,34 @@ static bool pair_shape(const SimDev &s) { return (s.nx & 1) == 0 && !s.solid && 
 
 int fluid_kernel_kind(const SimDev &s) { return (s.prec != LBIB_POP_F32 && pair_shape(s)) ? 1 : 0; }
 
+// SM count of the current device (cached per device).
+static int device_sms() {
+    static std::mutex mu;
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    return sms[dev];
+}
+
+// Prefetch distances (in blocks), measured at 256x128x128 and 512x256x256
+// on a GB300: 1.5 blocks per SM ahead for the one-cell kernel (5 resident
+// per SM), 3 per SM for the two-cells kernel (6 resident per SM).
 template <typename T>
 static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
+    const int sms = device_sms();
     if constexpr (sizeof(T) == 2) {
         if (pair_shape(s)) {
-            const int pblocks = (s.nf / 2 + FLUID_THREADS - 1) / FLUID_THREADS;
-            k_fluid_pair<T><<<pblocks, FLUID_THREADS, 0, st>>>(s, par, seed);
+            const int pblocks = (s.nf / 2 + PAIR_THREADS - 1) / PAIR_THREADS;
+            k_fluid_pair<T><<<pblocks, PAIR_THREADS, 0, st>>>(s, par, seed, 3 * sms);
             return;
         }
     }
     if (s.solid || s.in_on)
-        k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
+        k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed, 3 * sms / 2);
     else
-        k_fluid<T, false><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed);
+        k_fluid<T, false><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed, 3 * sms / 2);
 }
 
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st) {

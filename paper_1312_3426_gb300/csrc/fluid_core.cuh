@@ -317,6 +317,100 @@ __device__ __forceinline__ void inlet_cell(const SimDev &s, int x, int yl, int z
     h[18] = inlet_eq<18>(drho, rho, usq, u, sc);
 }
 
+// FP32 storage: the same BGK + Guo update written as an increment,
+// out = h + Delta, where every part of Delta is formed from quantities that
+// are small when the cell is near equilibrium, and the only rounding at the
+// scale of h is the final addition.  Per opposite pair (Q, Q+1), with
+// a = (h_Q - h_Q+1)/2, m = (h_Q + h_Q+1)/2 and j = sum h e (the momentum
+// of the stored deviations, without the force):
+//   odd   D_o = omega (3w e.j - a) + 3w e.G        (omega/2 + fpre = 1)
+//   even  D_e = omega (w (K + 4.5 rho (e.u)^2) - m) + fpre w (9 (e.u)(e.G) - 3 u.G)
+//   out_Q = h_Q + (D_e + D_o),  out_Q+1 = h_Q+1 + (D_e - D_o),
+// and for the rest population out_0 = h_0 + omega (w0 K - h_0) - 3 fpre w0 u.G,
+// with u = (j + G/2)/rho and K = drho - 1.5 rho u.u.  The product 3w e.j
+// and the subtraction of a are one FMA (a single rounding at the scale of
+// the non-equilibrium part), and 3w (1/6, 1/12) is applied as an unevaluated
+// FP32 pair hi + lo: FP32 rounding of 1/6 alone changes every cell's
+// momentum in the same direction by 3e-8 of itself per step, which the
+// driven channel integrates into a relative velocity bias ~200 times
+// larger.  Likewise the force is not added into j before it is rounded:
+// adding the same small G/2 to every cell's j rounds the same way in every
+// cell of a binade.
+struct Inc {
+    float sx, sy, sz;      // j
+    float ux, uy, uz;      // u
+    float Gx, Gy, Gz;      // force density of this step
+    float K, r45, m3uG;    // K, 4.5 rho, -3 u.G
+    float om, fpre;
+};
+
+constexpr double INC_C1 = 1.0 / 6.0;   // 3 w for |e|^2 = 1
+constexpr float INC_C1_HI = (float)INC_C1;
+constexpr float INC_C1_LO = (float)(INC_C1 - (double)INC_C1_HI);
+
+template <int Q>
+__device__ __forceinline__ void inc_pair(float *__restrict__ dst, uint32_t nfp, uint32_t f, float hq, float ho,
+                                         const Inc &c) {
+    constexpr bool axis = Q < 7;  // |e|^2 = 1; else 2 (weight and 3w halved, exactly)
+    constexpr float wq = axis ? (float)(1.0 / 18.0) : (float)(1.0 / 36.0);
+    constexpr float chi = axis ? INC_C1_HI : 0.5f * INC_C1_HI, clo = axis ? INC_C1_LO : 0.5f * INC_C1_LO;
+    const float a = 0.5f * __fsub_rn(hq, ho), m = 0.5f * __fadd_rn(hq, ho);
+    const float ej = edot<Q>(c.sx, c.sy, c.sz);
+    const float eu = edot<Q>(c.ux, c.uy, c.uz);
+    const float eG = edot<Q>(c.Gx, c.Gy, c.Gz);
+    float t = __fmaf_rn(chi, ej, -a);
+    t = __fmaf_rn(clo, ej, t);
+    const float Do = __fmaf_rn(c.om, t, __fmaf_rn(chi, eG, __fmul_rn(clo, eG)));
+    const float Aeq = __fmaf_rn(__fmul_rn(c.r45, wq), __fmul_rn(eu, eu), __fmul_rn(wq, c.K));
+    const float Fe = __fmul_rn(__fmul_rn(c.fpre, wq), __fmaf_rn(__fmul_rn(9.0f, eu), eG, c.m3uG));
+    const float De = __fmaf_rn(c.om, __fsub_rn(Aeq, m), Fe);
+    __stcs(dst + (uint32_t)Q * nfp + f, __fadd_rn(hq, __fadd_rn(De, Do)));
+    __stcs(dst + (uint32_t)(Q + 1) * nfp + f, __fadd_rn(ho, __fsub_rn(De, Do)));
+}
+
+// The increment-form collision and store of one FP32 cell from its pulled
+// populations h; returns u.u (the stability check) and sets u, rho.
+__device__ __forceinline__ float collide_increment(const SimDev &s, float *__restrict__ dst, uint32_t nfp, uint32_t f,
+                                                   const float (&h)[NQ], float Gx, float Gy, float Gz, float &ux,
+                                                   float &uy, float &uz, float &rho) {
+    const Moments mo = moments19(h);
+    Inc c;
+    c.om = s.omega;
+    c.fpre = s.fpre;
+    c.sx = mo.x;
+    c.sy = mo.y;
+    c.sz = mo.z;
+    c.Gx = Gx;
+    c.Gy = Gy;
+    c.Gz = Gz;
+    const float drho = mo.r;
+    rho = s.rho0 + drho;
+    const float irho = __fdividef(1.0f, rho);  // rho is near 1: the fast reciprocal is within 2 ulp
+    ux = fmaf(0.5f, Gx, mo.x) * irho;
+    uy = fmaf(0.5f, Gy, mo.y) * irho;
+    uz = fmaf(0.5f, Gz, mo.z) * irho;
+    c.ux = ux;
+    c.uy = uy;
+    c.uz = uz;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    c.m3uG = -3.0f * (ux * Gx + uy * Gy + uz * Gz);
+    c.K = fmaf(-1.5f * rho, usq, drho);
+    c.r45 = 4.5f * rho;
+    constexpr float w0 = (float)(1.0 / 3.0);
+    const float h0 = h[0];
+    __stcs(dst + f, __fadd_rn(h0, __fmaf_rn(c.om, __fmaf_rn(w0, c.K, -h0), __fmul_rn(c.fpre * w0, c.m3uG))));
+    inc_pair<1>(dst, nfp, f, h[1], h[2], c);
+    inc_pair<3>(dst, nfp, f, h[3], h[4], c);
+    inc_pair<5>(dst, nfp, f, h[5], h[6], c);
+    inc_pair<7>(dst, nfp, f, h[7], h[8], c);
+    inc_pair<9>(dst, nfp, f, h[9], h[10], c);
+    inc_pair<11>(dst, nfp, f, h[11], h[12], c);
+    inc_pair<13>(dst, nfp, f, h[13], h[14], c);
+    inc_pair<15>(dst, nfp, f, h[15], h[16], c);
+    inc_pair<17>(dst, nfp, f, h[17], h[18], c);
+    return usq;
+}
+
 // BC: the variant for simulations with obstacles or a velocity inlet (the
 // plain variant carries no test for either).
 template <typename T, bool BC>
@@ -348,6 +442,14 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
         Gy += g.y;
         Gz += g.z;
         s.G[par ^ 1][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    if constexpr (sizeof(T) == 4) {
+        float ux, uy, uz, rho;
+        const float usq = collide_increment(s, (float *)dst, nfp, f, h, Gx, Gy, Gz, ux, uy, uz, rho);
+        if (active) s.ufield[f] = make_float4(ux, uy, uz, rho);
+        if (!(usq < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
+        return;
     }
 
     // moments of the raw numbers, then back to deviations (exact: 2^-s)
@@ -646,6 +748,46 @@ __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uin
     LBIB_PULL2(14) LBIB_PULL2(15) LBIB_PULL2(16) LBIB_PULL2(17) LBIB_PULL2(18)
 #undef LBIB_PULL2
     pair_update<T>(s, par, f, P, step_seed);
+}
+
+// Pull offset of direction q in the fluid index space away from the
+// periodic edges and walls: cell f pulls population q from f - e_q.
+__host__ __device__ constexpr unsigned long long pack_e(int axis) {
+    unsigned long long p = 0;
+    for (int q = 0; q < NQ; ++q) {
+        const int e = axis == 0 ? d3q19_ex(q) : (axis == 1 ? d3q19_ey(q) : d3q19_ez(q));
+        p |= (unsigned long long)(e + 1) << (2 * q);
+    }
+    return p;
+}
+__device__ __forceinline__ int unpack_e(unsigned long long p, int q) { return (int)((p >> (2 * q)) & 3ull) - 1; }
+
+// L2 prefetch for a later block: thread q < 19 of block b asks the L2 to
+// fetch, with one bulk prefetch, the stretch of plane q that block b + pf
+// (of CELLS cells each) will pull, widened by 16 cells on each side and
+// clipped to the plane.  The blocks of a launch run roughly in index order,
+// so the DRAM requests run ahead of the warps that wait for them.  A
+// prefetch is a hint: it changes no result, and cells near the periodic
+// edges and walls (whose sources lie elsewhere) are fetched normally.
+template <int ESZ, int CELLS>
+__device__ __forceinline__ void prefetch_sources(const SimDev &s, const void *src, int pf) {
+    if (pf <= 0 || threadIdx.x >= NQ) return;
+    const long long fb = (long long)(blockIdx.x + pf) * CELLS;
+    if (fb >= s.nf) return;
+    const int q = (int)threadIdx.x;
+    constexpr unsigned long long PX = pack_e(0), PY = pack_e(1), PZ = pack_e(2);
+    const long long off = -((long long)unpack_e(PX, q) + (long long)s.nx * unpack_e(PY, q) +
+                            (long long)s.nx * s.nyf * unpack_e(PZ, q));
+    long long a = fb + off - 16, b = fb + CELLS + off + 16;
+    if (a < 0) a = 0;
+    if (b > s.nfp) b = s.nfp;
+    if (b <= a) return;
+    // 16-byte aligned start and size inside the plane (nfp is a multiple of 64)
+    const long long ab = (a * ESZ) & ~15ll;
+    long long bb = (b * ESZ + 15) & ~15ll;
+    if (bb > (long long)s.nfp * ESZ) bb = (long long)s.nfp * ESZ;
+    const char *p = (const char *)src + (long long)q * s.nfp * ESZ + ab;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)(bb - ab)) : "memory");
 }
 
 // Seed of the rounding bits of step t.

@@ -3,15 +3,13 @@ oracle on the same seeded inputs.
 
 Tolerances (FP32 path):
   * fluid velocity: relative L2 over fluid cells <= 1e-5;
-  * node positions: max-abs <= 1e-6 lattice units where the fluid is nearly
-    at rest (a deformed object relaxing in a resting fluid, 1000 steps).
-    Where the flow carries the objects, a node's position error is the
-    integral of the fluid-velocity error it is advected with, so the bound is
-    1e-6 lu + 1e-5 x (largest node displacement): the fluid bar carried over
-    the path.  FP32 storage of the populations leaves a systematic relative
-    velocity error of a few 1e-6 in a steady channel (round-to-nearest of
-    nearly constant values), i.e. ~1e-5 lu over the 1.5 lu the sphere
-    travels in 1000 steps.
+  * node positions: max-abs <= 1e-6 lattice units (NODE_BAR), in flowing
+    channels as in resting fluid.  The FP32 collision is written as an
+    increment with no systematic rounding (fluid_core.cuh), so the velocity
+    the nodes are carried with stays within ~2e-7 of the FP64 oracle's;
+    measured after 1000 steps of the 40x20x20 sphere channel: 2.4e-7 lu.
+    The two tests where objects touch (soft-sphere contact) widen the bar by
+    the contact's sensitivity (contact_tol).
 FP16/BF16 storage is measured against the FP64 oracle's same-step profile
 (the FP16-shifted form must stay within 1e-3 relative L2).
 """
@@ -54,13 +52,18 @@ def nodes_maxabs(g, o, n_obj):
     return worst
 
 
-def node_tol(scene, o):
-    """1e-6 lu plus the fluid bar (1e-5 relative) times the node displacement."""
+NODE_BAR = 1e-6  # lattice units
+
+
+def contact_tol(scene, o):
+    """Objects in soft-sphere contact: a position difference dx changes the
+    contact force by (n+1) dx / r relative, so the bar is widened by the
+    fluid bar (1e-5 relative) times the largest node displacement."""
     disp = 0.0
     start = oracle.Oracle.from_scene(scene)
     for oid in range(len(scene.objects)):
         disp = max(disp, float(np.abs(o.read_nodes(oid)[0] - start.read_nodes(oid)[0]).max()))
-    return 1e-6 + 1e-5 * disp
+    return NODE_BAR + 1e-5 * disp
 
 
 def run_pair(scene, steps, **kw):
@@ -79,8 +82,9 @@ def test_sphere_channel_1000_steps_matches_oracle():
     o, g = run_pair(sc, 1000)
     err_u = rel_l2(g.velocity(), o.velocity(), sc)
     err_x = nodes_maxabs(g, o, len(sc.objects))
+    print(f"\n40x20x20 sphere channel, 1000 steps: velocity rel L2 {err_u:.3e}, node max-abs {err_x:.3e} lu")
     assert err_u <= 1e-5, err_u
-    assert err_x <= node_tol(sc, o), (err_x, node_tol(sc, o))
+    assert err_x <= 1e-6, err_x
     # the object moved with the flow and deformed: the comparison is not trivial
     x0 = oracle.Oracle.from_scene(sc).read_nodes(0)[0]
     assert np.abs(o.read_nodes(0)[0] - x0).max() > 0.1
@@ -166,7 +170,7 @@ def test_ragged_box_two_templates_matches_oracle(walls):
     sc = _two_object_scene(walls)
     o, g = run_pair(sc, 300)
     assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
 
 
 def test_objects_crossing_the_periodic_boundary():
@@ -174,7 +178,7 @@ def test_objects_crossing_the_periodic_boundary():
     sc.objects[0].origin = (0.4, 9.1, 28.6)   # straddles x = 0 and z = nz
     o, g = run_pair(sc, 200)
     assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
 
 
 @pytest.mark.parametrize("overlap,cluster,mclusters,threads,chunk",
@@ -210,7 +214,7 @@ def test_launch_knobs_chunks_and_midrun_node_change(overlap, cluster, mclusters,
     advance(40)
     g.sync()
     assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
 
 
 def test_node_near_wall_drops_force_like_oracle():
@@ -218,7 +222,7 @@ def test_node_near_wall_drops_force_like_oracle():
     sc.objects[0].origin = (10.3, 3.2, 8.7)   # radius 3: nodes within 0.5 of the wall plane
     o, g = run_pair(sc, 50)
     assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
     d = g.dropped()
     assert np.abs(d).max() > 0
     # FP32 terms summed in FP64
@@ -289,7 +293,7 @@ def test_mass_conserved_fp64_reduction():
 def test_analyze_matches_oracle():
     sc = _two_object_scene(True)
     o, g = run_pair(sc, 100)
-    tol = node_tol(sc, o)
+    tol = NODE_BAR
     batch = g.objects_analyze()
     for oid in range(2):
         a = g.analyze(oid)
@@ -491,7 +495,7 @@ def test_batch_matches_oracle():
     lbib.lbib_batch_step([g.h for g in gs], 200)
     for s, o, g in zip(scs, ors, gs):
         assert rel_l2(g.velocity(), o.velocity(), s) <= 1e-5
-        assert nodes_maxabs(g, o, len(s.objects)) <= node_tol(s, o)
+        assert nodes_maxabs(g, o, len(s.objects)) <= NODE_BAR
 
 
 # ------------------------------------------------------------- errors (host-made, no device fault)
@@ -575,7 +579,7 @@ def test_repulsion_dynamics_match_oracle():
     # position difference dx changes the contact force by (n+1) dx / r
     # relative (about 10x at r ~ 0.2): the fluid bar is widened by that
     err_u, err_x = rel_l2(g.velocity(), o.velocity(), sc), nodes_maxabs(g, o, 2)
-    assert err_u <= 1e-4 and err_x <= node_tol(sc, o), (err_u, err_x, node_tol(sc, o))
+    assert err_u <= 1e-4 and err_x <= contact_tol(sc, o), (err_u, err_x, contact_tol(sc, o))
 
 
 def test_wall_repulsion_holds_an_object_like_the_oracle():
@@ -589,7 +593,7 @@ def test_wall_repulsion_holds_an_object_like_the_oracle():
     assert x[:, 1].min() > 1.0 and np.abs(o.repulsion_forces()).max() > 1e-5  # held above the plane
     # as above, with the wall term's (n+1)/d = 92 at the final gap d = 0.024
     err_u, err_x = rel_l2(g.velocity(), o.velocity(), sc), nodes_maxabs(g, o, 1)
-    assert err_u <= 1e-3 and err_x <= node_tol(sc, o), (err_u, err_x, node_tol(sc, o))
+    assert err_u <= 1e-3 and err_x <= contact_tol(sc, o), (err_u, err_x, contact_tol(sc, o))
 
 
 # ------------------------------------------------------------- velocity inlet (Sec. 6 inflow plane)
@@ -613,7 +617,7 @@ def test_velocity_inlet_matches_oracle():
     u = g.velocity()
     assert np.abs(u[:, 1, 1:13, 1:19] - np.array([0, 0, 0.01])[:, None, None]).max() < 1e-7
     assert rel_l2(u, o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
     assert np.abs(o.read_nodes(0)[0][:, 2].mean() - 12.0) > 0.05  # the cells were carried
 
 
@@ -644,7 +648,7 @@ def test_obstacles_match_oracle():
     u = g.velocity()
     assert np.abs(u[:, sc.solid]).max() == 0.0
     assert rel_l2(u, o.velocity(), sc) <= 1e-5
-    assert nodes_maxabs(g, o, 2) <= node_tol(sc, o)
+    assert nodes_maxabs(g, o, 2) <= NODE_BAR
     assert abs(g.mass() - o.fluid_totals()[0]) <= 1e-9 * o.fluid_totals()[0]
 
 
@@ -665,3 +669,35 @@ def test_batch_with_obstacles_equals_alone():
     for s, a, m in zip(scs, alone, mixed):
         ua, um = a.velocity(), m.velocity()
         assert np.abs(ua - um).max() <= 1e-5 * np.abs(ua).max()
+
+
+def test_batch_repulsion_changed_between_calls_equals_individual_steps():
+    """Repulsion switched on, then retuned, between batched calls of 32
+    steps (two captured 16-step chunks each): the batch must follow every
+    change as lbib_step does."""
+    def scene():
+        sc = _probe_scene([(8.0, 9.0, 9.0), (8.0 + 2 * 2.5 + 0.3, 9.0, 9.0), (16.0, 1.0 + 2.5 + 0.3, 9.0)],
+                          nx=32, friction=0.05, moduli=scenes.PAPER_MODULI, radius=2.5)
+        sc.objects[2].force = (0.0, -1e-4, 0.0)
+        return sc
+    settings = [None, ((5e-5, 2.0, 0.5), (1e-6, 1.2, 0.5)), ((2e-4, 2.0, 0.5), (4e-6, 1.2, 0.5))]
+    alone = lbib.Sim.from_scene(scene())
+    never = lbib.Sim.from_scene(scene())
+    mixed = [lbib.Sim.from_scene(scene()), lbib.Sim.from_scene(scenes.channel_sphere())]
+    for rep in settings:
+        if rep is not None:
+            lbib.lbib_set_repulsion(alone.h, *rep)
+            lbib.lbib_set_repulsion(mixed[0].h, *rep)
+        alone.step(32)
+        never.step(32)
+        lbib.lbib_batch_step([m.h for m in mixed], 32)
+        xa, _ = alone.read_nodes(-1)
+        xm, _ = mixed[0].read_nodes(-1)
+        xn, _ = never.read_nodes(-1)
+        assert np.abs(xa - xm).max() <= 1e-6
+        if rep is not None:
+            assert np.abs(xa - xn).max() > 1e-4  # the repulsion moved the nodes
+    # the only flow is the one the objects drive (|u| ~ 2e-4), so the order
+    # of the FP32 spreading atomics shows at a larger fraction of it
+    ua, um = alone.velocity(), mixed[0].velocity()
+    assert np.abs(ua - um).max() <= 1e-4 * np.abs(ua).max()
