@@ -318,7 +318,8 @@ LBIB_API lbib_status lbib_fluid_mass_noalloc(lbib_sim *sim, double *mass);
 /* Counts (oif_info, Sec. 5).  out[8] = n_templates, n_objects, n_nodes,
  * fluid cells, steps taken, device bytes held, precision, and the fluid
  * kernel the step uses: 0 one cell per thread; 1 two x-adjacent cells per
- * thread (16-bit storage, even nx, no obstacles, no inlet). */
+ * thread (16-bit storage, even nx, no obstacles, no inlet); 2 the
+ * warp-specialised two-cells kernel (see LBIB_TUNE_FLUID_KERNEL). */
 LBIB_API lbib_status lbib_info(const lbib_sim *sim, int64_t out[8]);
 
 /* Momentum the nodes would have given to solid corners (Sec. 2 spreading
@@ -382,14 +383,22 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * fluid kernel running beside it).  LBIB_TUNE_MEMBRANE_THREADS: threads per
  * block of the membrane-force kernel (a multiple of 32 in [32, 256],
  * default 192: fewer threads leave more of each SM to the fluid kernel
- * running beside it).  Results do not depend on the knobs beyond the order
- * of floating-point atomics.  LBIB_ERR_ARG for an unknown key or an
- * out-of-range value. */
+ * running beside it).  LBIB_TUNE_FLUID_KERNEL (16-bit storage): 0
+ * (default) and 1 the two-cells-per-thread kernel (where nx is even and
+ * there are no obstacles or inlet), 2 the warp-specialised two-cells kernel
+ * (a producer warp streams the populations through shared memory with bulk
+ * asynchronous copies; needs nx a multiple of 8 with a row segment of at
+ * least 64 cells, and no obstacles or inlet, else the step uses value 1;
+ * slower than value 1 on a GB300, kept for comparison); FP32 storage
+ * ignores it.  Results do not depend on the knobs beyond the order of
+ * floating-point atomics (the three 16-bit kernels give identical
+ * populations).  LBIB_ERR_ARG for an unknown key or an out-of-range value. */
 typedef enum {
     LBIB_TUNE_IB_CLUSTER = 0,
     LBIB_TUNE_OVERLAP = 1,
     LBIB_TUNE_MEMBRANE_CLUSTERS = 2,
-    LBIB_TUNE_MEMBRANE_THREADS = 3
+    LBIB_TUNE_MEMBRANE_THREADS = 3,
+    LBIB_TUNE_FLUID_KERNEL = 4
 } lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);

@@ -1162,6 +1162,11 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         s->membrane_clusters = value;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_FLUID_KERNEL) {
+        if (value < 0 || value > 2) return fail(s, LBIB_ERR_ARG, "fluid kernel must be 0, 1 or 2");
+        s->d.fkern = value;
+        return LBIB_OK;
+    }
     return fail(s, LBIB_ERR_ARG, "unknown tuning key");
 }
 
@@ -1181,6 +1186,10 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
     }
     if (key == LBIB_TUNE_MEMBRANE_CLUSTERS) {
         *value = s->membrane_clusters;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_FLUID_KERNEL) {
+        *value = s->d.fkern;
         return LBIB_OK;
     }
     return LBIB_ERR_ARG;

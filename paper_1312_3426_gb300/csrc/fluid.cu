@@ -43,7 +43,15 @@ __global__ void __launch_bounds__(PAIR_THREADS, 6) k_fluid_pair(SimDev s, int pa
 
 static bool pair_shape(const SimDev &s) { return (s.nx & 1) == 0 && !s.solid && !s.in_on; }
 
-int fluid_kernel_kind(const SimDev &s) { return (s.prec != LBIB_POP_F32 && pair_shape(s)) ? 1 : 0; }
+// The warp-specialised kernel is opt-in (LBIB_TUNE_FLUID_KERNEL = 2): on
+// a GB300 it ran slower than the two-cells kernel with L2 prefetch (0.0947
+// vs 0.0882 ms in the step at 256x128x128, 0.764 vs 0.709 ms at
+// 512x256x256) and slowed the membrane kernel beside it.
+int fluid_kernel_kind(const SimDev &s) {
+    if (s.prec == LBIB_POP_F32 || !pair_shape(s)) return 0;
+    if (s.fkern == 2 && fluid_tma_shape(s)) return 2;
+    return 1;
+}
 
 // SM count of the current device (cached per device).
 static int device_sms() {
@@ -63,6 +71,10 @@ template <typename T>
 static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
     const int sms = device_sms();
     if constexpr (sizeof(T) == 2) {
+        if (fluid_kernel_kind(s) == 2) {
+            launch_fluid_tma(s, par, seed, st);
+            return;
+        }
         if (pair_shape(s)) {
             const int pblocks = (s.nf / 2 + PAIR_THREADS - 1) / PAIR_THREADS;
             k_fluid_pair<T><<<pblocks, PAIR_THREADS, 0, st>>>(s, par, seed, 3 * sms);

@@ -685,12 +685,12 @@ __device__ __forceinline__ void collide2(uint32_t *__restrict__ dst, uint32_t nf
 
 // Collision and store of the cell pair (f, f+1) from its pulled populations
 // P (packed pairs, low half: cell f).
+// act: the active-cell bits of f (bit 0) and f + 1 (bit 1).
 template <typename T>
-__device__ __forceinline__ void pair_update(const SimDev &s, int par, uint32_t f, const uint32_t (&P)[NQ],
-                                            uint32_t step_seed) {
+__device__ __forceinline__ void pair_update_act(const SimDev &s, int par, uint32_t f, const uint32_t (&P)[NQ],
+                                                uint32_t step_seed, uint32_t act) {
     uint32_t *__restrict__ dst = (uint32_t *)s.pop[par ^ 1];
     const uint32_t nfp = (uint32_t)s.nfp;
-    const uint32_t act = (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u;
     float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
     if (act & 1u) {  // spread force of this step; clear the buffer of the next
         ga = __ldcg(s.G[par] + f);
@@ -728,6 +728,12 @@ __device__ __forceinline__ void pair_update(const SimDev &s, int par, uint32_t f
     if (act & 1u) s.ufield[f] = make_float4(c.ux.x, c.uy.x, c.uz.x, rho.x);
     if (act & 2u) s.ufield[f + 1] = make_float4(c.ux.y, c.uy.y, c.uz.y, rho.y);
     if (!(usq.x < 0.09f) || !(usq.y < 0.09f)) atomicOr(s.status, ST_UNSTABLE);
+}
+
+template <typename T>
+__device__ __forceinline__ void pair_update(const SimDev &s, int par, uint32_t f, const uint32_t (&P)[NQ],
+                                            uint32_t step_seed) {
+    pair_update_act<T>(s, par, f, P, step_seed, (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u);
 }
 
 template <typename T>

@@ -158,6 +158,9 @@ struct SimDev {
     // like the wall rows
     const uint32_t *solid;
     int nsolid;
+    // 16-bit storage: fluid kernel preference (0 the fastest that fits the
+    // shape, 1 two cells per thread, 2 the warp-specialised two-cells kernel)
+    int fkern;
 };
 
 #ifdef __CUDACC__
@@ -188,7 +191,12 @@ struct SmemAttr {
 
 // ---- launchers (fluid.cu) -------------------------------------------------
 cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);
-int fluid_kernel_kind(const SimDev &s);  // the kernel launch_fluid picks (lbib_info out[7])
+// the kernel launch_fluid picks (lbib_info out[7]): 0 one cell per thread,
+// 1 two cells per thread, 2 warp-specialised two cells per thread
+int fluid_kernel_kind(const SimDev &s);
+// fluid_tma.cu: the warp-specialised kernel and whether the shape allows it
+bool fluid_tma_shape(const SimDev &s);
+cudaError_t launch_fluid_tma(const SimDev &s, int par, uint32_t seed, cudaStream_t st);
 cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
                           cudaStream_t st);
 cudaError_t launch_read_coupling(const SimDev &s, int gpar, float *g_full, cudaStream_t st);

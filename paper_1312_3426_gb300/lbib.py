@@ -305,6 +305,7 @@ LBIB_TUNE_IB_CLUSTER = 0
 LBIB_TUNE_OVERLAP = 1
 LBIB_TUNE_MEMBRANE_CLUSTERS = 2
 LBIB_TUNE_MEMBRANE_THREADS = 3
+LBIB_TUNE_FLUID_KERNEL = 4
 
 
 def lbib_set_tuning(h, key, value):

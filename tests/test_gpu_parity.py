@@ -396,6 +396,27 @@ def test_shifted_half_storage_poiseuille_error(prec, bound):
     assert rel_l2(g32.velocity(), o32.velocity(), sc) < err
 
 
+def tma_width(nx):
+    """Row segment of the warp-specialised kernel (0: the shape does not fit)."""
+    if nx % 8:
+        return 0
+    return next(W for W in range(256, 7, -8) if nx % W == 0)
+
+
+def expected_kind(nx, kernel):
+    return 2 if kernel == 2 and tma_width(nx) >= 64 else 1
+
+
+def run_pair_kernel(sc, steps, kernel, **kw):
+    o = oracle.Oracle.from_scene(sc)
+    o.step(steps)
+    g = lbib.Sim.from_scene(sc, **kw)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_FLUID_KERNEL, kernel)
+    g.step(steps)
+    g.sync()
+    return o, g
+
+
 @pytest.mark.parametrize("prec,bound", [("f16s", 5e-3), ("bf16s", 5e-2)])
 @pytest.mark.parametrize("walls", [True, False])
 def test_half_storage_two_cells_per_thread(prec, bound, walls):
@@ -410,29 +431,57 @@ def test_half_storage_two_cells_per_thread(prec, bound, walls):
     assert nodes_maxabs(g, o, 2) <= 1e-3
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("prec,bound", [("f16s", 5e-3), ("bf16s", 5e-2)])
 @pytest.mark.parametrize("nx,ny,nz,walls,objects,steps", [
     (32, 19, 29, True, True, 300),
     (64, 19, 29, False, True, 300),    # periodic y
     (8, 12, 7, True, False, 400),      # 4 pairs per row
     (2, 9, 6, False, False, 400),      # one pair per row: both x wraps in every pair
-    (512, 6, 5, True, False, 300),
+    (512, 6, 5, True, False, 300),     # two 256-cell segments per row
     (46, 11, 170, True, False, 200),
+    (72, 13, 9, True, True, 300),      # one 72-cell segment per row
+    (384, 7, 6, False, False, 300),    # three 128-cell segments per row
 ])
-def test_half_storage_two_cells_per_thread_shapes(prec, bound, nx, ny, nz, walls, objects, steps):
-    """The two-cells-per-thread kernel over row widths from one pair to 256
-    pairs: wall rows and the periodic wraps in x, y and z against the
-    oracle, and the total mass."""
+def test_half_storage_two_cells_per_thread_shapes(kernel, prec, bound, nx, ny, nz, walls, objects, steps):
+    """The two-cells kernels (kernel 1: one pair per thread; kernel 2: the
+    warp-specialised one, where the shape allows it, else kernel 1) over
+    row widths from one pair to 256 pairs: wall rows and the periodic wraps
+    in x, y and z against the oracle, and the total mass."""
     if objects:
         sc = _two_object_scene(walls, nx=nx, ny=ny, nz=nz)
     else:
         sc = scenes.Scene("rows", nx, ny, nz, walls=walls, tau=0.8, body_force=(2e-5, 0.0, 1e-5), steps=steps)
-    o, g = run_pair(sc, steps, precision=prec, pop_scale_log2=12)
-    assert int(g.info()[7]) == 1
+    o, g = run_pair_kernel(sc, steps, kernel, precision=prec, pop_scale_log2=12)
+    assert int(g.info()[7]) == expected_kind(nx, kernel)
     assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
     if objects:
         assert nodes_maxabs(g, o, 2) <= 1e-3
     assert abs(g.mass() - o.fluid_totals()[0]) <= 1e-5 * o.fluid_totals()[0]
+
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+@pytest.mark.parametrize("nx,ny,nz,walls", [(256, 20, 12, True), (64, 18, 10, False), (512, 12, 6, True),
+                                            (192, 22, 14, True), (72, 16, 9, True), (1024, 5, 4, False)])
+def test_warp_specialised_kernel_equals_two_cells_kernel(prec, nx, ny, nz, walls):
+    """Without objects the step is deterministic, so the warp-specialised
+    kernel must store exactly the populations of the one-pair-per-thread
+    kernel (same arithmetic, same rounding bits), step after step."""
+    assert tma_width(nx) >= 64
+    sc = scenes.Scene("rows", nx, ny, nz, walls=walls, tau=0.8, body_force=(2e-5, 1e-6, 1e-5), steps=40)
+    a = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=12)
+    b = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=12)
+    lbib.lbib_set_tuning(a.h, lbib.LBIB_TUNE_FLUID_KERNEL, 1)
+    lbib.lbib_set_tuning(b.h, lbib.LBIB_TUNE_FLUID_KERNEL, 2)
+    assert int(a.info()[7]) == 1 and int(b.info()[7]) == 2
+    for _ in range(2):
+        a.step(20)
+        b.step(20)
+        pa, pb = a.populations(), b.populations()
+        assert np.abs(pa).max() > 0
+        assert np.array_equal(pa, pb)
+    a.close()
+    b.close()
 
 
 # ------------------------------------------------------------- batching
