@@ -49,6 +49,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LB+IB MLUPS & %HBM roofline, FP32 vs FP16-store; serving p50/p99 vs plain"
 BYTES_PER_CELL = {"f32": 152, "f16s": 76, "bf16s": 76}
+FLUID_KERNELS = ("k_fluid", "k_fluid_pair", "k_fluid_pair_tma")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -69,9 +70,15 @@ def parse_args():
                     help="membrane forces overlapped with the fluid step (-1: library default)")
     ap.add_argument("--membrane-clusters", type=int, default=-1,
                     help="clusters of the membrane kernel (0: one per object, -1: library default)")
+    ap.add_argument("--fluid-kernel", type=int, default=-1, choices=(-1, 0, 1, 2),
+                    help="16-bit fluid kernel (-1: library default; see LBIB_TUNE_FLUID_KERNEL)")
     ap.add_argument("--launch", choices=["separate", "batched"], default="separate",
                     help="lbib_step, or lbib_batch_step (work lists + captured graphs) on the one simulation")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP32 / FP16-shifted / BF16-shifted records (both RBC channels, Poiseuille error)")
+    ap.add_argument("--no-poiseuille", action="store_true",
+                    help="skip the Poiseuille errors (20,000 steps of the object-free 512x256x256 channel per storage)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-mlups-estimate", type=float, default=22000.0,
                     help="batched FP16 throughput used to set the arrival rate (offered load 0.8)")
@@ -318,6 +325,168 @@ def batch_workload(args, lbib, torch, dev, stream):
                                                             for k, v in timing.items()}}
 
 
+def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier, e2e=True, launch="separate",
+            clocks=False):
+    """Times args.steps steps of scene `sc` with `precision` storage after
+    args.warmup untimed ones (CUDA events on the simulation's stream,
+    barrier + synchronize on both sides, max over ranks), with per-kernel
+    events on every n-th step (n = steps / 8, at most 16, so the fluid
+    kernel's mean rests on at least 8 launches); then, with `e2e`, the host
+    loop of e2e_record.  Returns the numbers of the JSON line."""
+    sim = lbib.Sim.from_scene(sc, precision=precision, pop_scale_log2=args.scale_log2, stream=stream.cuda_stream)
+    nf = sc.n_fluid_cells
+    if args.ib_cluster:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
+    if args.overlap >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
+    if args.membrane_clusters >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
+    if args.fluid_kernel >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_FLUID_KERNEL, args.fluid_kernel)
+    kernel = FLUID_KERNELS[int(sim.info()[7])]
+    sim.step(max(3, args.warmup))
+    sim.sync()
+    sampler = None
+    if clocks:
+        try:
+            uuid = str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            uuid = None
+        sampler = ClockSampler(uuid)
+    barrier()
+    if sampler:
+        sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    persistent = launch == "batched"
+    if not persistent:
+        lbib.lbib_profile_enable(sim.h, profile_every(args.steps))
+    e0.record(stream)
+    if persistent:
+        lbib.lbib_batch_step([sim.h], args.steps)
+    else:
+        sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    clk = sampler.stop() if sampler else None
+    prof = lbib.lbib_profile_read(sim.h) if not persistent else None
+    lbib.lbib_profile_enable(sim.h, False)
+    sim.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    if prof is not None:
+        fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
+        nodes_ms = prof["nodes_ms"] / max(1, prof["nodes_launches"])
+        membrane_ms = prof["membrane_ms"] / max(1, prof["membrane_launches"])
+        launches = int(prof["fluid_launches"])
+    else:  # one fused launch per step: the whole step is the kernel
+        fluid_ms, nodes_ms, membrane_ms, launches = ms / args.steps, 0.0, 0.0, args.steps
+    rec = None
+    if e2e:
+        nobj = len(sc.objects)
+        fh = torch.zeros((max(nobj, 1), 3), dtype=torch.float64, pin_memory=True).numpy()
+        out = torch.zeros((max(nobj, 1), 14), dtype=torch.float64, pin_memory=True).numpy()
+        k_e2e = args.steps
+        # (1) pipelined host loop: every step uploads its forces, steps and
+        # enqueues its analysis; the host reads step k's analysis (two
+        # page-locked slots) after enqueueing step k + 1, so the device does
+        # not wait for the host between steps
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(k_e2e):
+            lbib.lbib_objects_set_force(sim.h, fh[:nobj]) if nobj else None
+            sim.step(1)
+            lbib.lbib_objects_analyze_async(sim.h, k & 1)
+            if k > 0:
+                lbib.lbib_objects_analyze_wait(sim.h, (k - 1) & 1, nobj, out)
+        lbib.lbib_objects_analyze_wait(sim.h, (k_e2e - 1) & 1, nobj, out)
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        # (2) the same loop waiting for every step's analysis before the next
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            if nobj:
+                lbib.lbib_objects_set_force(sim.h, fh[:nobj])
+            sim.step(1)
+            if nobj:
+                lbib.lbib_objects_analyze(sim.h, nobj, out[:nobj])
+            else:
+                sim.sync()
+        barrier()
+        dt_sync = max_over_ranks(time.perf_counter() - t0, dev)
+        rec = e2e_record(nf, k_e2e, dt, dt_sync, world, nobj)
+    sim.close()
+    return {"ms": ms, "value": whole_job_mlups(nf, args.steps, ms, world), "fluid_ms": fluid_ms,
+            "nodes_ms": nodes_ms, "membrane_ms": membrane_ms, "fluid_launches": launches, "kernel": kernel,
+            "clocks": clk, "e2e": rec}
+
+
+def profile_every(steps):
+    """Per-kernel events on every n-th step: n = steps / 8 (at most 16), so
+    that at least 8 fluid launches are timed even in a short run."""
+    return max(1, min(16, steps // 8))
+
+
+GOLDEN_PROFILE = os.path.join(ROOT, "tests", "golden", "channel_512x256x256_profile.txt")
+
+
+def poiseuille_errors(args, lbib, precisions):
+    """Relative L2 of each storage precision's velocity field against the
+    FP64 oracle's profile, on the object-free 512x256x256 channel (walls in
+    y, tau = 1, body force 1e-5) after 20,000 steps from rest, and the drift
+    of its total mass.  The reference profile u_x(y) is the committed file
+    tests/golden/channel_512x256x256_profile.txt (written by the oracle;
+    the flow is invariant along x and z, and u_y = u_z = 0)."""
+    nx, ny, nz, steps = 512, 256, 256, 20000
+    prof = np.loadtxt(GOLDEN_PROFILE)
+    out = {"steps": steps, "reference": "tests/golden/channel_512x256x256_profile.txt (FP64 oracle)"}
+    for prec in precisions:
+        g = lbib.Sim(nx, ny, nz, walls=True, tau=1.0, rho0=1.0, body_force=(1e-5, 0.0, 0.0), friction=0.05,
+                     precision=prec, pop_scale_log2=0 if prec == "f32" else args.scale_log2)
+        g.fluid_init()
+        m0 = g.mass()
+        g.step(steps)
+        m1 = g.mass()
+        u = g.velocity()
+        g.close()
+        num = float(np.sum((u[0][:, 1:ny - 1, :].astype(np.float64) - prof[None, 1:ny - 1, None]) ** 2))
+        num += float(np.sum(u[1][:, 1:ny - 1, :].astype(np.float64) ** 2) + np.sum(u[2][:, 1:ny - 1, :].astype(np.float64) ** 2))
+        den = float(np.sum(prof[1:ny - 1] ** 2)) * nx * nz
+        out[prec] = {"rel_l2": float(f"{(num / den) ** 0.5:.4g}"), "mass_drift": float(f"{abs(m1 - m0) / m0:.3g}")}
+    return out
+
+
+def precision_records(args, lbib, torch, stream, dev, local, world, barrier, peak, main):
+    """The FP32 / FP16-shifted / BF16-shifted comparison: MLUPS, the fluid
+    kernel's roofline and the end-to-end loop for each storage on the
+    256x128x128 channel with 200 cells (the main line's workload) and on the
+    512x256x256 channel with 2000 cells, and the Poiseuille error of each
+    against the FP64 oracle (object-free 512x256x256 channel)."""
+    out = {}
+    for wl in ("rbc256", "rbc512"):
+        sc = make_scene(wl)
+        rows = {}
+        for prec in ("f32", "f16s", "bf16s"):
+            if wl == args.workload and prec == args.precision and args.launch == "separate":
+                m = main
+            else:
+                m = measure(args, lbib, torch, sc, prec, stream, dev, local, world, barrier,
+                            e2e=(wl == "rbc256" and not args.no_e2e))
+            bpc = BYTES_PER_CELL[prec]
+            ach = bpc * sc.n_fluid_cells / (m["fluid_ms"] / 1e3) / 1e9
+            rows[prec] = {"value": round(m["value"], 2), "unit": "MLUPS", "ms_per_step": round(m["ms"] / args.steps, 5),
+                          "roofline": {"kernel": f"{m['kernel']}<{prec}>", "bytes_per_cell": bpc,
+                                       "mean_launch_ms": round(m["fluid_ms"], 5), "launches_timed": m["fluid_launches"],
+                                       "achieved": round(ach, 1), "frac": round(ach / peak, 4)},
+                          "step_hbm_frac": round((bpc * sc.n_fluid_cells + 400 * sc.n_nodes) / (m["ms"] / args.steps / 1e3)
+                                                 / 1e9 / peak, 4),
+                          "e2e": m["e2e"]["value"] if m["e2e"] else None}
+        out[workload_desc(sc)] = rows
+    if not args.no_poiseuille:
+        out["poiseuille_512x256x256"] = poiseuille_errors(args, lbib, ("f32", "f16s", "bf16s"))
+    return out
+
+
 def serving_comparison(args, stream):
     """The request trace served by continuous batching and by the plain
     one-at-a-time loop (same trace, FP16-shifted storage, 150 GB budget)."""
@@ -403,94 +572,18 @@ def main():
         return
 
     sc = make_scene(args.workload)
-    sim = lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
-                              stream=stream.cuda_stream)
-    nf = sc.n_fluid_cells
-    if args.ib_cluster:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
-    if args.overlap >= 0:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
-    if args.membrane_clusters >= 0:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
-    fluid_kernel = ("k_fluid", "k_fluid_pair")[int(sim.info()[7])]
-    sim.step(max(3, args.warmup))
-    sim.sync()
-
-    try:
-        uuid = str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:
-        uuid = None
-    sampler = ClockSampler(uuid)
-    barrier()
-    sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    persistent = args.launch == "batched"
-    if not persistent:
-        # timing events on every 16th step: the kernel durations are sampled
-        # over the whole timed region without putting events into every step
-        lbib.lbib_profile_enable(sim.h, 16)
-    e0.record(stream)
-    if persistent:
-        lbib.lbib_batch_step([sim.h], args.steps)
-    else:
-        sim.step(args.steps)
-    e1.record(stream)
-    barrier()
-    clocks = sampler.stop()
-    prof = lbib.lbib_profile_read(sim.h) if not persistent else None
-    lbib.lbib_profile_enable(sim.h, False)
-    sim.sync()
-    ms = max_over_ranks(e0.elapsed_time(e1), dev)
-    value = whole_job_mlups(nf, args.steps, ms, world)
-
-    if prof is not None:
-        fluid_ms = prof["fluid_ms"] / max(1, prof["fluid_launches"])
-        nodes_ms = prof["nodes_ms"] / max(1, prof["nodes_launches"])
-        membrane_ms = prof["membrane_ms"] / max(1, prof["membrane_launches"])
-    else:  # one fused launch per step: the whole step is the kernel
-        fluid_ms = ms / args.steps
-        nodes_ms = membrane_ms = 0.0
     peak, peak_kind = measured_peak()
-    bpc = BYTES_PER_CELL[args.precision]
+    m = measure(args, lbib, torch, sc, args.precision, stream, dev, local, world, barrier, e2e=not args.no_e2e,
+                launch=args.launch, clocks=True)
+    ms, value, nf, bpc = m["ms"], m["value"], sc.n_fluid_cells, BYTES_PER_CELL[args.precision]
+    fluid_ms, nodes_ms, membrane_ms = m["fluid_ms"], m["nodes_ms"], m["membrane_ms"]
     achieved = bpc * nf / (fluid_ms / 1e3) / 1e9
     traffic = profiled_traffic(args.workload, args.precision, nf)
+    clocks, e2e, persistent = m["clocks"], m["e2e"], args.launch == "batched"
 
-    e2e = None
-    if not args.no_e2e:
-        nobj = len(sc.objects)
-        fh = torch.zeros((max(nobj, 1), 3), dtype=torch.float64, pin_memory=True).numpy()
-        out = torch.zeros((max(nobj, 1), 14), dtype=torch.float64, pin_memory=True).numpy()
-        k_e2e = args.steps
-        # (1) pipelined host loop: every step uploads its forces, steps and
-        # enqueues its analysis; the host reads step k's analysis (two
-        # page-locked slots) after enqueueing step k + 1, so the device does
-        # not wait for the host between steps
-        barrier()
-        t0 = time.perf_counter()
-        for k in range(k_e2e):
-            lbib.lbib_objects_set_force(sim.h, fh[:nobj]) if nobj else None
-            sim.step(1)
-            lbib.lbib_objects_analyze_async(sim.h, k & 1)
-            if k > 0:
-                lbib.lbib_objects_analyze_wait(sim.h, (k - 1) & 1, nobj, out)
-        lbib.lbib_objects_analyze_wait(sim.h, (k_e2e - 1) & 1, nobj, out)
-        barrier()
-        dt = max_over_ranks(time.perf_counter() - t0, dev)
-        # (2) the same loop waiting for every step's analysis before the next
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            if nobj:
-                lbib.lbib_objects_set_force(sim.h, fh[:nobj])
-            sim.step(1)
-            if nobj:
-                lbib.lbib_objects_analyze(sim.h, nobj, out[:nobj])
-            else:
-                sim.sync()
-        barrier()
-        dt_sync = max_over_ranks(time.perf_counter() - t0, dev)
-        e2e = e2e_record(nf, k_e2e, dt, dt_sync, world, nobj)
+    precision = None
+    if not args.no_precision:
+        precision = precision_records(args, lbib, torch, stream, dev, local, world, barrier, peak, m)
 
     serving = None
     if world == 1 and not args.no_serving:
@@ -512,9 +605,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"{fluid_kernel}<{args.precision}>",
-                         "bytes_per_cell": bpc,
-                         "mean_launch_ms": round(fluid_ms, 5), "peak_source": peak_kind + " copy bandwidth"},
+                         "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"{m['kernel']}<{args.precision}>",
+                         "bytes_per_cell": bpc, "mean_launch_ms": round(fluid_ms, 5),
+                         "launches_timed": m["fluid_launches"], "peak_source": peak_kind + " copy bandwidth"},
             "step_breakdown_ms": {"fluid": round(fluid_ms, 5), "nodes": round(nodes_ms, 5),
                                   "membrane_overlapped": round(membrane_ms, 5)},
             "nodes_per_s": round(world * sc.n_nodes * args.steps / (ms / 1e3), 1),
@@ -526,10 +619,10 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": base,
+            "precision": precision,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -109,3 +109,30 @@ def test_e2e_record_keys():
     assert r["unit"] == "MLUPS" and r["h2d_bytes_per_step"] == 2400 and r["d2h_bytes_per_step"] == 22404
     assert r["value"] == round(bench.whole_job_mlups(4_000_000, 100, 20.0, 1), 2)
     assert r["synchronous_value"] < r["value"]
+
+
+def test_profile_sampling_gives_eight_fluid_launches():
+    """The per-kernel events sample every n-th step with n = steps / 8 (at
+    most 16): the fluid kernel's mean rests on at least 8 launches from 8
+    steps on, whatever step count the timed region starts at."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for steps in (8, 10, 20, 64, 127, 128, 129, 1000, 4000):
+        n = bench.profile_every(steps)
+        assert 1 <= n <= 16
+        for start in range(n):
+            sampled = sum(1 for t in range(start, start + steps) if t % n == 0)
+            assert sampled >= 8, (steps, n, start, sampled)
+    assert bench.profile_every(4000) == 16 and bench.profile_every(20) == 2
+
+
+def test_poiseuille_reference_profile_is_readable():
+    """The bench's Poiseuille reference is the committed oracle profile:
+    256 values, zero at the walls, peak near 0.184."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    u = np.loadtxt(bench.GOLDEN_PROFILE)
+    assert u.shape == (256,) and u[0] == 0.0 and u[-1] == 0.0
+    assert 0.18 < u.max() < 0.19
