@@ -320,9 +320,7 @@ def batch_workload(args, lbib, torch, dev, stream):
     nodes = sum(sc.n_nodes for sc in scs)
     for s in sims:
         s.close()
-    return scs, cells, nodes, ms, clocks, {"ib_cluster": choice[0], "overlap": choice[1], "membrane_threads": choice[2],
-                                           "candidates_s": {"/".join(map(str, k)): round(v, 5)
-                                                            for k, v in timing.items()}}
+    return scs, cells, nodes, ms, clocks, dict(choice, candidates_s={k: round(v, 5) for k, v in timing.items()})
 
 
 def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier, e2e=True, launch="separate",

@@ -389,8 +389,11 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * (a producer warp streams the populations through shared memory with bulk
  * asynchronous copies; needs nx a multiple of 8 with a row segment of at
  * least 64 cells, and no obstacles or inlet, else the step uses value 1;
- * slower than value 1 on a GB300, kept for comparison); FP32 storage
- * ignores it.  Results do not depend on the knobs beyond the order of
+ * slower than value 1 on a GB300, kept for comparison; lbib_batch_step runs
+ * value 1 instead), 3 one cell per thread; FP32 storage ignores it.
+ * LBIB_TUNE_NODE_THREADS: nodes per block of the node-update kernel (32,
+ * 64, 128 or 256, default 256; lbib_batch_step takes the first
+ * simulation's).  Results do not depend on the knobs beyond the order of
  * floating-point atomics (the three 16-bit kernels give identical
  * populations).  LBIB_ERR_ARG for an unknown key or an out-of-range value. */
 typedef enum {
@@ -398,7 +401,8 @@ typedef enum {
     LBIB_TUNE_OVERLAP = 1,
     LBIB_TUNE_MEMBRANE_CLUSTERS = 2,
     LBIB_TUNE_MEMBRANE_THREADS = 3,
-    LBIB_TUNE_FLUID_KERNEL = 4
+    LBIB_TUNE_FLUID_KERNEL = 4,
+    LBIB_TUNE_NODE_THREADS = 5
 } lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);

@@ -39,10 +39,23 @@ extern __shared__ float batch_smem[];
 
 // One launch per storage type and boundary-condition variant present in the
 // batch (items grouped by both; BC: obstacles or an inlet).
+// L2 prefetch of the sources of work item blockIdx.x + pf of the same
+// launch (items of one launch run roughly in index order); CELLS cells per
+// item.
+template <int ESZ, int CELLS>
+__device__ __forceinline__ void prefetch_item(const SimDev *__restrict__ sims, const long long *__restrict__ t_base,
+                                              int step_off, const int2 *__restrict__ items, int pf) {
+    if (threadIdx.x >= NQ || (int)(blockIdx.x + pf) >= (int)gridDim.x) return;
+    const int2 it = items[blockIdx.x + pf];
+    const SimDev &s = sims[it.x];
+    prefetch_cells<ESZ, CELLS>(s, s.pop[(t_base[it.x] + step_off) & 1], (long long)it.y * CELLS);
+}
+
 template <typename T, bool BC>
 __global__ void __launch_bounds__(FLUID_THREADS, 5)
     k_batch_fluid(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
-                  const int2 *__restrict__ items) {
+                  const int2 *__restrict__ items, int pf) {
+    prefetch_item<sizeof(T), FLUID_THREADS>(sims, t_base, step_off, items, pf);
     const int2 it = items[blockIdx.x];  // (simulation, block of cells)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
@@ -53,7 +66,8 @@ __global__ void __launch_bounds__(FLUID_THREADS, 5)
 template <typename T>
 __global__ void __launch_bounds__(FLUID_THREADS, 3)
     k_batch_fluid_pair(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
-                       const int2 *__restrict__ items) {
+                       const int2 *__restrict__ items, int pf) {
+    prefetch_item<2, 2 * FLUID_THREADS>(sims, t_base, step_off, items, pf);
     const int2 it = items[blockIdx.x];  // (simulation, block of FLUID_THREADS cell pairs)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
@@ -61,7 +75,9 @@ __global__ void __launch_bounds__(FLUID_THREADS, 3)
     if (f < s.nf) fluid_pair<T>(s, (int)(t & 1), f, step_seed(t));
 }
 
-__global__ void __launch_bounds__(IB_THREADS, 3)
+// NT nodes per work item (the plan's node chunk)
+template <int NT>
+__global__ void __launch_bounds__(NT, 768 / NT)
     k_batch_nodes(const SimDev *__restrict__ sims, const long long *__restrict__ t_base, int step_off,
                   const int2 *__restrict__ items) {
     const int2 it = items[blockIdx.x];  // (simulation, first node)
@@ -90,13 +106,14 @@ struct BatchPlan {
     std::vector<uint64_t> serial;  // identity of each simulation (addresses can be reused)
     std::vector<int> nobj, nn, group;  // group: fluid kernel variant (2 * precision + BC)
     std::vector<SimDev> dev;  // descriptors the device copy holds
-    int cluster = 0, device = -1, mthreads = IB_THREADS;
+    int cluster = 0, device = -1, mthreads = IB_THREADS, nthreads = IB_THREADS_DEFAULT;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
     int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
     int n_flp[8] = {};  // fluid items per kernel variant (see fluid_group)
     int n_fl = 0, n_nd = 0, n_mb = 0;
     int max_nodes = 0;
+    int pf_cell = 0, pf_pair = 0;  // L2 prefetch distances of the fluid launches (work items)
     cudaStream_t aux = nullptr;   // membrane kernel
     cudaStream_t gst = nullptr;   // graph launches (the caller's stream may be the legacy one, which cannot be captured)
     cudaEvent_t ev_nodes = nullptr, ev_membrane = nullptr, ev_join = nullptr;
@@ -132,12 +149,14 @@ static std::mutex g_plan_mu;
 // kernels of FP16 / BF16 storage (even nx, plain boundaries).
 static int fluid_group(const lbib_sim *s) {
     const bool bc = s->d.solid || s->d.in_on;
-    if (s->d.prec != LBIB_POP_F32 && (s->d.nx & 1) == 0 && !bc) return 6 + (s->d.prec - 1);
+    if (s->d.prec != LBIB_POP_F32 && (s->d.nx & 1) == 0 && !bc && s->d.fkern != 3) return 6 + (s->d.prec - 1);
     return 2 * s->d.prec + (bc ? 1 : 0);
 }
 
 static bool plan_matches(lbib_sim *const *sims, int n, int cluster) {
-    if ((int)g_plan.sims.size() != n || g_plan.cluster != cluster || g_plan.device != sims[0]->device) return false;
+    if ((int)g_plan.sims.size() != n || g_plan.cluster != cluster || g_plan.device != sims[0]->device ||
+        g_plan.nthreads != sims[0]->node_threads)
+        return false;
     for (int i = 0; i < n; ++i)
         if (g_plan.sims[i] != sims[i] || g_plan.serial[i] != sims[i]->serial ||
             g_plan.nobj[i] != (int)sims[i]->objs.size() || g_plan.group[i] != fluid_group(sims[i]) ||
@@ -153,6 +172,7 @@ static cudaError_t set_membrane_attrs(size_t smem) {
 
 static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStream_t st) {
     g_plan.release();
+    const int nthreads = sims[0]->node_threads;  // node chunk of the batch
     if (!g_plan.aux) {
         int lo = 0, hi = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -172,11 +192,17 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
         const int blocks = (s->d.nf + cells_per_block - 1) / cells_per_block;
         for (int b = 0; b < blocks; ++b) flp[grp].push_back(make_int2(i, b));
         if (!s->objs.empty()) {
-            for (int f = 0; f < s->nn_total; f += IB_THREADS) nd.push_back(make_int2(i, f));
+            for (int f = 0; f < s->nn_total; f += nthreads) nd.push_back(make_int2(i, f));
             for (int o = 0; o < (int)s->objs.size(); ++o) mb.push_back(make_int2(i, o));
             max_nodes = std::max(max_nodes, s->max_nodes);
         }
     }
+    // largest objects first: their clusters start in the first wave and the
+    // small ones fill in behind them (longest-processing-time-first order),
+    // so a level-4 cell does not start late and set the launch's tail
+    std::stable_sort(mb.begin(), mb.end(), [&](const int2 &a, const int2 &b) {
+        return sims[a.x]->objs[a.y].nn > sims[b.x]->objs[b.y].nn;
+    });
     for (int k = 0; k < 8; ++k) {
         g_plan.n_flp[k] = (int)flp[k].size();
         fl.insert(fl.end(), flp[k].begin(), flp[k].end());
@@ -204,7 +230,14 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
     g_plan.n_nd = (int)nd.size();
     g_plan.n_mb = (int)mb.size();
     g_plan.cluster = cluster;
+    g_plan.nthreads = nthreads;
     g_plan.device = sims[0]->device;
+    {
+        int sms = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g_plan.device)) != cudaSuccess) return e;
+        g_plan.pf_cell = 3 * sms / 2;  // 1.5 blocks per SM ahead (5 resident)
+        g_plan.pf_pair = sms;          // 1 block per SM ahead (3 resident)
+    }
     g_plan.max_nodes = max_nodes;
     return g_plan.n_mb ? set_membrane_attrs(ib_smem_bytes(max_nodes)) : cudaSuccess;
 }
@@ -247,7 +280,12 @@ static cudaError_t enqueue_steps(cudaStream_t st, int step_off, int k) {
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
         const int off = step_off + j;
         if (g_plan.n_nd) {
-            k_batch_nodes<<<g_plan.n_nd, IB_THREADS, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd);
+            switch (g_plan.nthreads) {
+                case 32: k_batch_nodes<32><<<g_plan.n_nd, 32, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd); break;
+                case 64: k_batch_nodes<64><<<g_plan.n_nd, 64, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd); break;
+                case 128: k_batch_nodes<128><<<g_plan.n_nd, 128, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd); break;
+                default: k_batch_nodes<256><<<g_plan.n_nd, 256, 0, st>>>(g_plan.d_sims, g_plan.d_t, off, nd); break;
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) break;
             if ((e = cudaEventRecord(g_plan.ev_nodes, st)) != cudaSuccess) break;
             if ((e = cudaStreamWaitEvent(g_plan.aux, g_plan.ev_nodes, 0)) != cudaSuccess) break;
@@ -259,21 +297,23 @@ static cudaError_t enqueue_steps(cudaStream_t st, int step_off, int k) {
             const int *n = g_plan.n_flp;
             const SimDev *ds = g_plan.d_sims;
             const long long *dt = g_plan.d_t;
-            if (n[0]) k_batch_fluid<float, false><<<n[0], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            // prefetch distances as in the single-simulation launches
+            const int p1 = g_plan.pf_cell, p2 = g_plan.pf_pair;
+            if (n[0]) k_batch_fluid<float, false><<<n[0], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[0];
-            if (n[1]) k_batch_fluid<float, true><<<n[1], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[1]) k_batch_fluid<float, true><<<n[1], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[1];
-            if (n[2]) k_batch_fluid<__half, false><<<n[2], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[2]) k_batch_fluid<__half, false><<<n[2], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[2];
-            if (n[3]) k_batch_fluid<__half, true><<<n[3], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[3]) k_batch_fluid<__half, true><<<n[3], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[3];
-            if (n[4]) k_batch_fluid<__nv_bfloat16, false><<<n[4], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[4]) k_batch_fluid<__nv_bfloat16, false><<<n[4], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[4];
-            if (n[5]) k_batch_fluid<__nv_bfloat16, true><<<n[5], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[5]) k_batch_fluid<__nv_bfloat16, true><<<n[5], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p1);
             g += n[5];
-            if (n[6]) k_batch_fluid_pair<__half><<<n[6], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[6]) k_batch_fluid_pair<__half><<<n[6], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p2);
             g += n[6];
-            if (n[7]) k_batch_fluid_pair<__nv_bfloat16><<<n[7], FLUID_THREADS, 0, st>>>(ds, dt, off, g);
+            if (n[7]) k_batch_fluid_pair<__nv_bfloat16><<<n[7], FLUID_THREADS, 0, st>>>(ds, dt, off, g, p2);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (g_plan.n_nd) e = cudaStreamWaitEvent(st, g_plan.ev_membrane, 0);

@@ -811,7 +811,7 @@ lbib_status lbib_step(lbib_sim *s, int n) {
             if (r != LBIB_OK) return r;
             LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
         }
-        if (objects) LBIB_CUDA(s, launch_nodes(s->d, par, s->stream), "node update");
+        if (objects) LBIB_CUDA(s, launch_nodes(s->d, par, s->node_threads, s->stream), "node update");
         if (objects && s->overlap) {
             LBIB_CUDA(s, cudaEventRecord(s->ev_nodes, s->stream), "event");
             LBIB_CUDA(s, cudaStreamWaitEvent(s->aux, s->ev_nodes, 0), "event");
@@ -1163,8 +1163,14 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         return LBIB_OK;
     }
     if (key == LBIB_TUNE_FLUID_KERNEL) {
-        if (value < 0 || value > 2) return fail(s, LBIB_ERR_ARG, "fluid kernel must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(s, LBIB_ERR_ARG, "fluid kernel must be 0, 1, 2 or 3");
         s->d.fkern = value;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_NODE_THREADS) {
+        if (value != 32 && value != 64 && value != 128 && value != 256)
+            return fail(s, LBIB_ERR_ARG, "node threads must be 32, 64, 128 or 256");
+        s->node_threads = value;
         return LBIB_OK;
     }
     return fail(s, LBIB_ERR_ARG, "unknown tuning key");
@@ -1190,6 +1196,10 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
     }
     if (key == LBIB_TUNE_FLUID_KERNEL) {
         *value = s->d.fkern;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_NODE_THREADS) {
+        *value = s->node_threads;
         return LBIB_OK;
     }
     return LBIB_ERR_ARG;

@@ -48,7 +48,7 @@ static bool pair_shape(const SimDev &s) { return (s.nx & 1) == 0 && !s.solid && 
 // vs 0.0882 ms in the step at 256x128x128, 0.764 vs 0.709 ms at
 // 512x256x256) and slowed the membrane kernel beside it.
 int fluid_kernel_kind(const SimDev &s) {
-    if (s.prec == LBIB_POP_F32 || !pair_shape(s)) return 0;
+    if (s.prec == LBIB_POP_F32 || !pair_shape(s) || s.fkern == 3) return 0;
     if (s.fkern == 2 && fluid_tma_shape(s)) return 2;
     return 1;
 }
@@ -75,7 +75,7 @@ static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, 
             launch_fluid_tma(s, par, seed, st);
             return;
         }
-        if (pair_shape(s)) {
+        if (fluid_kernel_kind(s) == 1) {
             const int pblocks = (s.nf / 2 + PAIR_THREADS - 1) / PAIR_THREADS;
             k_fluid_pair<T><<<pblocks, PAIR_THREADS, 0, st>>>(s, par, seed, 3 * sms);
             return;

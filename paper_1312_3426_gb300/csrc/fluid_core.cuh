@@ -768,17 +768,10 @@ __host__ __device__ constexpr unsigned long long pack_e(int axis) {
 }
 __device__ __forceinline__ int unpack_e(unsigned long long p, int q) { return (int)((p >> (2 * q)) & 3ull) - 1; }
 
-// L2 prefetch for a later block: thread q < 19 of block b asks the L2 to
-// fetch, with one bulk prefetch, the stretch of plane q that block b + pf
-// (of CELLS cells each) will pull, widened by 16 cells on each side and
-// clipped to the plane.  The blocks of a launch run roughly in index order,
-// so the DRAM requests run ahead of the warps that wait for them.  A
-// prefetch is a hint: it changes no result, and cells near the periodic
-// edges and walls (whose sources lie elsewhere) are fetched normally.
+// The bulk L2 prefetch of the stretches of every plane that the CELLS cells
+// from fb on pull (thread q < 19 takes plane q).
 template <int ESZ, int CELLS>
-__device__ __forceinline__ void prefetch_sources(const SimDev &s, const void *src, int pf) {
-    if (pf <= 0 || threadIdx.x >= NQ) return;
-    const long long fb = (long long)(blockIdx.x + pf) * CELLS;
+__device__ __forceinline__ void prefetch_cells(const SimDev &s, const void *src, long long fb) {
     if (fb >= s.nf) return;
     const int q = (int)threadIdx.x;
     constexpr unsigned long long PX = pack_e(0), PY = pack_e(1), PZ = pack_e(2);
@@ -794,6 +787,19 @@ __device__ __forceinline__ void prefetch_sources(const SimDev &s, const void *sr
     if (bb > (long long)s.nfp * ESZ) bb = (long long)s.nfp * ESZ;
     const char *p = (const char *)src + (long long)q * s.nfp * ESZ + ab;
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)(bb - ab)) : "memory");
+}
+
+// L2 prefetch for a later block: thread q < 19 of block b asks the L2 to
+// fetch, with one bulk prefetch, the stretch of plane q that block b + pf
+// (of CELLS cells each) will pull, widened by 16 cells on each side and
+// clipped to the plane.  The blocks of a launch run roughly in index order,
+// so the DRAM requests run ahead of the warps that wait for them.  A
+// prefetch is a hint: it changes no result, and cells near the periodic
+// edges and walls (whose sources lie elsewhere) are fetched normally.
+template <int ESZ, int CELLS>
+__device__ __forceinline__ void prefetch_sources(const SimDev &s, const void *src, int pf) {
+    if (pf <= 0 || threadIdx.x >= NQ) return;
+    prefetch_cells<ESZ, CELLS>(s, src, (long long)(blockIdx.x + pf) * CELLS);
 }
 
 // Seed of the rounding bits of step t.

@@ -16,8 +16,10 @@ __global__ void __launch_bounds__(IB_THREADS, 4) k_membrane(SimDev s) {
     for (int o = (int)(blockIdx.x / C); o < s.nobj; o += n_clusters) membrane_object(s, o, ib_smem);
 }
 
-__global__ void __launch_bounds__(IB_THREADS, 4) k_nodes(SimDev s, int par) {
-    const int i = blockIdx.x * IB_THREADS + threadIdx.x;
+// NT nodes per block (LBIB_TUNE_NODE_THREADS: 32, 64, 128 or 256)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_nodes(SimDev s, int par) {
+    const int i = blockIdx.x * NT + threadIdx.x;
     if (i < s.nn_total) node_step(s, i, par);
 }
 
@@ -44,9 +46,16 @@ cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max
     return cudaLaunchKernelEx(&cfg, k_membrane, s);
 }
 
-cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st) {
+cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st) {
     if (s.nn_total == 0) return cudaSuccess;
-    k_nodes<<<(s.nn_total + IB_THREADS - 1) / IB_THREADS, IB_THREADS, 0, st>>>(s, par);
+    const int blocks = (s.nn_total + threads - 1) / threads;
+    switch (threads) {
+        case 32: k_nodes<32><<<blocks, 32, 0, st>>>(s, par); break;
+        case 64: k_nodes<64><<<blocks, 64, 0, st>>>(s, par); break;
+        case 128: k_nodes<128><<<blocks, 128, 0, st>>>(s, par); break;
+        case 256: k_nodes<256><<<blocks, 256, 0, st>>>(s, par); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -40,7 +40,8 @@ namespace lbib {
 
 constexpr int NQ = 19;
 constexpr int FLUID_THREADS = 256;
-constexpr int IB_THREADS = 256;
+constexpr int IB_THREADS = 256;          // largest block of the object kernels
+constexpr int IB_THREADS_DEFAULT = 256;  // node kernel block (LBIB_TUNE_NODE_THREADS)
 constexpr int MAX_TEMPLATE_NODES = 5120;  // 11 floats of shared memory per node
 constexpr int ACTIVE_RESET_STEPS = 128;    // period of the active-cell re-marking
 
@@ -158,8 +159,9 @@ struct SimDev {
     // like the wall rows
     const uint32_t *solid;
     int nsolid;
-    // 16-bit storage: fluid kernel preference (0 the fastest that fits the
-    // shape, 1 two cells per thread, 2 the warp-specialised two-cells kernel)
+    // 16-bit storage: fluid kernel preference (0 and 1 two cells per thread
+    // where the shape allows, 2 the warp-specialised two-cells kernel, 3 one
+    // cell per thread)
     int fkern;
 };
 
@@ -218,7 +220,7 @@ cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int
 // threads: block size (a multiple of 32, at most IB_THREADS)
 cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads,
                             cudaStream_t st);
-cudaError_t launch_nodes(const SimDev &s, int par, cudaStream_t st);
+cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st);
 // object-object repulsion added to Fel (after the membrane kernel, which
 // also writes the object bounding boxes); max_nodes sizes shared memory
 cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st);

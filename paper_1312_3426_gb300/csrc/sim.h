@@ -74,6 +74,7 @@ struct lbib_sim {
     bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
     int membrane_threads = 192;         // block size of the membrane kernel
+    int node_threads = lbib::IB_THREADS_DEFAULT;  // nodes per block of the node kernel
 
     double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects
     double rep_wall[3] = {0, 1, 0};     // and against the walls

@@ -1,15 +1,24 @@
 """Autotuner for the launch-shape knobs of the C ABI.
 
 The knobs (``lbib_set_tuning``) change no result beyond the order of
-floating-point atomics, only the speed: the thread blocks per object of the
-membrane-force kernel (``LBIB_TUNE_IB_CLUSTER``), its block size
-(``LBIB_TUNE_MEMBRANE_THREADS``) and whether that kernel overlaps the fluid
-kernel on a second stream (``LBIB_TUNE_OVERLAP``).
+floating-point atomics, only the speed:
+
+* ``LBIB_TUNE_IB_CLUSTER``      thread blocks per object of the membrane kernel;
+* ``LBIB_TUNE_OVERLAP``         membrane kernel beside the fluid kernel (second stream);
+* ``LBIB_TUNE_MEMBRANE_THREADS`` block size of the membrane kernel;
+* ``LBIB_TUNE_NODE_THREADS``    nodes per block of the node kernel (the node chunk);
+* ``LBIB_TUNE_FLUID_KERNEL``    16-bit storage: two cells per thread (1), the
+  warp-specialised two-cells kernel (2, single simulations only) or one
+  cell per thread (3).
+
 ``autotune`` times a few steps of the caller's own simulations for each
-candidate and keeps the fastest; results are cached by a key of the
-workload's shape (box-size class, storage precision, largest template), so
-simulations of the same class reuse the choice.  Tuning advances the
-simulations it times; callers tune on a throw-away copy or accept the steps.
+candidate and keeps the fastest, one knob group at a time (membrane shape
+first, then the node chunk, then the fluid kernel, each group searched with
+the best choice of the groups before it).  Results are cached by a key of
+the workload's shape (number of simulations, box-size class, node-count
+class, storage precisions, batched or not), so simulations of the same class
+reuse the choice.  Tuning advances the simulations it times; callers tune on
+a throw-away copy or accept the steps.
 """
 from __future__ import annotations
 
@@ -19,14 +28,19 @@ from . import lbib
 
 _CACHE: dict = {}
 
+KNOBS = (("cluster", lbib.LBIB_TUNE_IB_CLUSTER), ("overlap", lbib.LBIB_TUNE_OVERLAP),
+         ("membrane_threads", lbib.LBIB_TUNE_MEMBRANE_THREADS), ("node_threads", lbib.LBIB_TUNE_NODE_THREADS),
+         ("fluid_kernel", lbib.LBIB_TUNE_FLUID_KERNEL))
+DEFAULT = {"cluster": 1, "overlap": 1, "membrane_threads": 192, "node_threads": 256, "fluid_kernel": 0}
 
-def _key(sims):
+
+def _key(sims, batched):
     infos = [s.info() for s in sims]
     cells = sum(int(i[3]) for i in infos)
     nodes = sum(int(i[2]) for i in infos)
     prec = sorted({int(i[6]) for i in infos})
     cls = lambda v: 0 if v <= 0 else int(round(float(v) ** 0.5).bit_length())  # noqa: E731
-    return (len(sims), cls(cells), cls(nodes), tuple(prec))
+    return (len(sims), cls(cells), cls(nodes), tuple(prec), bool(batched))
 
 
 def _time(sims, steps, batched):
@@ -48,35 +62,49 @@ def _time(sims, steps, batched):
     return time.perf_counter() - t0
 
 
-def autotune(sims, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), steps=32, batched=None):
-    """Chooses and applies the fastest (cluster, overlap, membrane threads)
-    for `sims` (Sim objects); returns the choice and the measured seconds
-    per candidate."""
+def apply(sims, choice):
+    """Sets every knob of `choice` (a dict with the keys of DEFAULT)."""
+    for s in sims:
+        for name, key in KNOBS:
+            lbib.lbib_set_tuning(s.h, key, int(choice[name]))
+
+
+def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), node_threads=(64, 128, 256)):
+    """The knob groups searched, in order: [(name, ...), [values, ...]]."""
+    groups = []
+    has_objects = any(int(s.info()[1]) > 0 for s in sims)
+    if has_objects:
+        groups.append((("cluster", "overlap", "membrane_threads"),
+                       [(c, o, t) for c in clusters for o in overlaps for t in threads]))
+        groups.append((("node_threads",), [(t,) for t in node_threads]))
+    if any(int(s.info()[6]) != lbib.LBIB_POP_F32 for s in sims):
+        kernels = (1, 3) if batched else (1, 2, 3)
+        groups.append((("fluid_kernel",), [(k,) for k in kernels]))
+    return groups
+
+
+def autotune(sims, steps=32, batched=None, **search):
+    """Chooses and applies the fastest knobs for `sims` (Sim objects);
+    returns (choice, seconds per candidate): choice is a dict with the keys
+    of DEFAULT, the timing dict is keyed by 'name=value,...' strings."""
     sims = list(sims)
     if batched is None:
         batched = len(sims) > 1
-    key = _key(sims) + (batched,)
+    key = _key(sims, batched)
     if key in _CACHE:
-        best = _CACHE[key][0]
-        _apply(sims, *best)
+        apply(sims, _CACHE[key][0])
         return _CACHE[key]
-    if not any(s.obj_tid for s in sims):
-        best, timing = (1, 1, 192), {}
-    else:
-        timing = {}
-        for c in clusters:
-            for ov in overlaps:
-                for th in threads:
-                    _apply(sims, c, ov, th)
-                    timing[(c, ov, th)] = _time(sims, steps, batched)
-        best = min(timing, key=timing.get)
-    _apply(sims, *best)
+    best = dict(DEFAULT)
+    timing = {}
+    for names, values in candidates(sims, batched, **search):
+        group_t = {}
+        for vals in values:
+            trial = dict(best, **dict(zip(names, vals)))
+            apply(sims, trial)
+            t = _time(sims, steps, batched)
+            group_t[vals] = t
+            timing[",".join(f"{n}={v}" for n, v in zip(names, vals))] = t
+        best.update(dict(zip(names, min(group_t, key=group_t.get))))
+    apply(sims, best)
     _CACHE[key] = (best, timing)
     return _CACHE[key]
-
-
-def _apply(sims, cluster, overlap, threads=192):
-    for s in sims:
-        lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_IB_CLUSTER, cluster)
-        lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_OVERLAP, overlap)
-        lbib.lbib_set_tuning(s.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, threads)

@@ -750,3 +750,41 @@ def test_batch_repulsion_changed_between_calls_equals_individual_steps():
     # of the FP32 spreading atomics shows at a larger fraction of it
     ua, um = alone.velocity(), mixed[0].velocity()
     assert np.abs(ua - um).max() <= 1e-4 * np.abs(ua).max()
+
+
+def test_node_chunk_knob_single_and_batched():
+    """Nodes per block of the node kernel (LBIB_TUNE_NODE_THREADS) changes
+    nothing beyond the order of the spreading atomics, alone and batched."""
+    sc = _two_object_scene(True)
+    a = lbib.Sim.from_scene(sc)
+    b = lbib.Sim.from_scene(sc)
+    lbib.lbib_set_tuning(b.h, lbib.LBIB_TUNE_NODE_THREADS, 64)
+    assert lbib.lbib_get_tuning(b.h, lbib.LBIB_TUNE_NODE_THREADS) == 64
+    a.step(100)
+    b.step(100)
+    ua, ub = a.velocity(), b.velocity()
+    assert np.abs(ua - ub).max() <= 1e-5 * np.abs(ua).max()
+    assert np.abs(a.read_nodes(-1)[0] - b.read_nodes(-1)[0]).max() <= 1e-6
+    # batched with a 32-node chunk (item boundaries inside objects)
+    c = [lbib.Sim.from_scene(s) for s in (sc, scenes.channel_sphere())]
+    lbib.lbib_set_tuning(c[0].h, lbib.LBIB_TUNE_NODE_THREADS, 32)
+    lbib.lbib_batch_step([x.h for x in c], 100)
+    assert np.abs(ua - c[0].velocity()).max() <= 1e-5 * np.abs(ua).max()
+    assert np.abs(a.read_nodes(-1)[0] - c[0].read_nodes(-1)[0]).max() <= 1e-6
+    for bad in (0, 16, 33, 96, 512):
+        with pytest.raises(lbib.LbibError):
+            lbib.lbib_set_tuning(a.h, lbib.LBIB_TUNE_NODE_THREADS, bad)
+
+
+@pytest.mark.parametrize("prec,bound", [("f16s", 5e-3), ("bf16s", 5e-2)])
+def test_one_cell_per_thread_knob_for_16_bit_storage(prec, bound):
+    """LBIB_TUNE_FLUID_KERNEL = 3 runs the one-cell kernel on a box the
+    two-cells kernel would take, alone and batched, within the 16-bit bar."""
+    sc = _two_object_scene(True, nx=38, ny=19, nz=29)
+    o, g = run_pair_kernel(sc, 300, 3, precision=prec, pop_scale_log2=12)
+    assert int(g.info()[7]) == 0
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+    h = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=12)
+    lbib.lbib_set_tuning(h.h, lbib.LBIB_TUNE_FLUID_KERNEL, 3)
+    lbib.lbib_batch_step([h.h], 300)
+    assert rel_l2(h.velocity(), o.velocity(), sc) <= bound

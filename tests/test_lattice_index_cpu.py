@@ -140,3 +140,4 @@ def test_corners_of_interior_points_are_the_expected_cells(driver):
     # the solid row and the halo loses its solid rows
     r = run(driver, box, True, np.array([[5.7, 1.2, 4.9]], np.float32))
     assert r["corner_refs"] == 4 and r["halo_refs"] == 32
+
