@@ -70,7 +70,10 @@ def parse_args():
                     help="membrane forces overlapped with the fluid step (-1: library default)")
     ap.add_argument("--membrane-clusters", type=int, default=-1,
                     help="clusters of the membrane kernel (0: one per object, -1: library default)")
-    ap.add_argument("--fluid-kernel", type=int, default=-1, choices=(-1, 0, 1, 2),
+    ap.add_argument("--membrane-threads", type=int, default=0,
+                    help="block size of the membrane kernel (0: library default)")
+    ap.add_argument("--node-threads", type=int, default=0, help="nodes per block of the node kernel (0: default)")
+    ap.add_argument("--fluid-kernel", type=int, default=-1, choices=(-1, 0, 1, 2, 3),
                     help="16-bit fluid kernel (-1: library default; see LBIB_TUNE_FLUID_KERNEL)")
     ap.add_argument("--launch", choices=["separate", "batched"], default="separate",
                     help="lbib_step, or lbib_batch_step (work lists + captured graphs) on the one simulation")
@@ -341,6 +344,10 @@ def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
     if args.fluid_kernel >= 0:
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_FLUID_KERNEL, args.fluid_kernel)
+    if args.membrane_threads:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, args.membrane_threads)
+    if args.node_threads:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_NODE_THREADS, args.node_threads)
     kernel = FLUID_KERNELS[int(sim.info()[7])]
     sim.step(max(3, args.warmup))
     sim.sync()
