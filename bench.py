@@ -73,6 +73,9 @@ def parse_args():
     ap.add_argument("--membrane-threads", type=int, default=0,
                     help="block size of the membrane kernel (0: library default)")
     ap.add_argument("--node-threads", type=int, default=0, help="nodes per block of the node kernel (0: default)")
+    ap.add_argument("--membrane-group", type=int, default=0, help="objects per membrane block (0: library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's launch shapes (and the flags above) instead of autotuning them")
     ap.add_argument("--fluid-kernel", type=int, default=-1, choices=(-1, 0, 1, 2, 3),
                     help="16-bit fluid kernel (-1: library default; see LBIB_TUNE_FLUID_KERNEL)")
     ap.add_argument("--launch", choices=["separate", "batched"], default="separate",
@@ -348,6 +351,17 @@ def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, args.membrane_threads)
     if args.node_threads:
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_NODE_THREADS, args.node_threads)
+    if args.membrane_group:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, args.membrane_group)
+    tuning = None
+    explicit = (args.ib_cluster or args.overlap >= 0 or args.membrane_clusters >= 0 or args.fluid_kernel >= 0
+                or args.membrane_threads or args.node_threads or args.membrane_group)
+    if not args.no_autotune and not explicit:
+        # the project's autotuner picks the launch shapes on this simulation
+        # (it advances it: part of the warm-up)
+        from paper_1312_3426_gb300 import tune
+        choice, timing = tune.autotune([sim], steps=128, batched=launch == "batched")
+        tuning = dict(choice, candidates_s={k: round(v, 5) for k, v in timing.items()})
     kernel = FLUID_KERNELS[int(sim.info()[7])]
     sim.step(max(3, args.warmup))
     sim.sync()
@@ -423,7 +437,7 @@ def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier
     sim.close()
     return {"ms": ms, "value": whole_job_mlups(nf, args.steps, ms, world), "fluid_ms": fluid_ms,
             "nodes_ms": nodes_ms, "membrane_ms": membrane_ms, "fluid_launches": launches, "kernel": kernel,
-            "clocks": clk, "e2e": rec}
+            "clocks": clk, "e2e": rec, "tuning": tuning}
 
 
 def profile_every(steps):
@@ -485,7 +499,8 @@ def precision_records(args, lbib, torch, stream, dev, local, world, barrier, pea
                                        "achieved": round(ach, 1), "frac": round(ach / peak, 4)},
                           "step_hbm_frac": round((bpc * sc.n_fluid_cells + 400 * sc.n_nodes) / (m["ms"] / args.steps / 1e3)
                                                  / 1e9 / peak, 4),
-                          "e2e": m["e2e"]["value"] if m["e2e"] else None}
+                          "e2e": m["e2e"]["value"] if m["e2e"] else None,
+                          "tuning": {k: v for k, v in (m["tuning"] or {}).items() if k != "candidates_s"} or None}
         out[workload_desc(sc)] = rows
     if not args.no_poiseuille:
         out["poiseuille_512x256x256"] = poiseuille_errors(args, lbib, ("f32", "f16s", "bf16s"))
@@ -607,7 +622,7 @@ def main():
             "config": {"workload": workload_desc(sc), "precision_storage": args.precision,
                        "fluid_cells": nf, "nodes": sc.n_nodes, "objects": len(sc.objects),
                        "l2": "inputs larger than L2 (populations %.0f MB), no flush" % (bpc * nf / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU", "tuning": m["tuning"]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": f"k_batch_fluid<{args.precision}>" if persistent else f"{m['kernel']}<{args.precision}>",

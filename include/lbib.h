@@ -393,7 +393,12 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * value 1 instead), 3 one cell per thread; FP32 storage ignores it.
  * LBIB_TUNE_NODE_THREADS: nodes per block of the node-update kernel (32,
  * 64, 128 or 256, default 256; lbib_batch_step takes the first
- * simulation's).  Results do not depend on the knobs beyond the order of
+ * simulation's).  LBIB_TUNE_MEMBRANE_GROUP: objects per block of the
+ * membrane-force kernel (1..15, default 1); above 1 each object gets
+ * LBIB_TUNE_MEMBRANE_THREADS threads of a block of group x threads threads
+ * (at most 1024) and the cluster knobs do not apply; the step fails with
+ * LBIB_ERR_CUDA when the block does not fit (threads or shared memory).
+ * lbib_batch_step ignores it.  Results do not depend on the knobs beyond the order of
  * floating-point atomics (the three 16-bit kernels give identical
  * populations).  LBIB_ERR_ARG for an unknown key or an out-of-range value. */
 typedef enum {
@@ -402,7 +407,8 @@ typedef enum {
     LBIB_TUNE_MEMBRANE_CLUSTERS = 2,
     LBIB_TUNE_MEMBRANE_THREADS = 3,
     LBIB_TUNE_FLUID_KERNEL = 4,
-    LBIB_TUNE_NODE_THREADS = 5
+    LBIB_TUNE_NODE_THREADS = 5,
+    LBIB_TUNE_MEMBRANE_GROUP = 6
 } lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);

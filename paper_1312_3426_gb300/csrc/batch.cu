@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(IB_THREADS, 4)
     k_batch_membrane(const SimDev *__restrict__ sims, const int2 *__restrict__ items) {
     cg::cluster_group cl = cg::this_cluster();
     const int2 it = items[blockIdx.x / cl.num_blocks()];  // (simulation, object)
-    membrane_object(sims[it.x], it.y, batch_smem);
+    membrane_object(sims[it.x], it.y, batch_smem, ClusterTeam());
 }
 
 __global__ void k_batch_advance(long long *t_base, int n, int steps) {

@@ -768,7 +768,8 @@ static lbib_status launch_membrane_timed(lbib_sim *s, cudaStream_t st) {
         if (r != LBIB_OK) return r;
         LBIB_CUDA(s, cudaEventRecord(ev[0], st), "profile event");
     }
-    LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, s->membrane_threads, st), "membrane forces");
+    LBIB_CUDA(s, launch_membrane(s->d, s->max_nodes, s->cluster, s->membrane_clusters, s->membrane_threads,
+                                 s->membrane_group, st), "membrane forces");
     LBIB_CUDA(s, launch_repulsion(s->d, s->max_nodes, st), "repulsion");
     if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], st), "profile event");
     return LBIB_OK;
@@ -1167,6 +1168,11 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         s->d.fkern = value;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_MEMBRANE_GROUP) {
+        if (value < 1 || value > 15) return fail(s, LBIB_ERR_ARG, "membrane group must be in [1, 15]");
+        s->membrane_group = value;
+        return LBIB_OK;
+    }
     if (key == LBIB_TUNE_NODE_THREADS) {
         if (value != 32 && value != 64 && value != 128 && value != 256)
             return fail(s, LBIB_ERR_ARG, "node threads must be 32, 64, 128 or 256");
@@ -1200,6 +1206,10 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
     }
     if (key == LBIB_TUNE_NODE_THREADS) {
         *value = s->node_threads;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_MEMBRANE_GROUP) {
+        *value = s->membrane_group;
         return LBIB_OK;
     }
     return LBIB_ERR_ARG;

@@ -10,10 +10,22 @@ extern __shared__ float ib_smem[];
 // Cluster c takes objects c, c + n_clusters, ... (a grid smaller than the
 // object count leaves SMs to the fluid kernel that runs beside it).
 __global__ void __launch_bounds__(IB_THREADS, 4) k_membrane(SimDev s) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int C = (int)cl.num_blocks();
+    const ClusterTeam tm;
+    const int C = tm.ranks();
     const int n_clusters = (int)(gridDim.x / C);
-    for (int o = (int)(blockIdx.x / C); o < s.nobj; o += n_clusters) membrane_object(s, o, ib_smem);
+    for (int o = (int)(blockIdx.x / C); o < s.nobj; o += n_clusters) membrane_object(s, o, ib_smem, tm);
+}
+
+// Several objects per block: group g (threads [g T, (g + 1) T)) of block b
+// takes object b G + g with its own shared memory and named barrier g + 1.
+// A few dense blocks hold a few SMs for a short time, where one block per
+// object would hold a slot on almost every SM while the fluid kernel runs.
+__global__ void __launch_bounds__(1024, 1) k_membrane_groups(SimDev s, int T, int group_floats) {
+    const int g = (int)threadIdx.x / T, G = (int)blockDim.x / T;
+    const int o = (int)blockIdx.x * G + g;
+    if (o >= s.nobj) return;  // whole groups only: no barrier is shared with another group
+    const GroupTeam tm{(int)threadIdx.x - g * T, T, g + 1};
+    membrane_object(s, o, ib_smem + (size_t)g * group_floats, tm);
 }
 
 // NT nodes per block (LBIB_TUNE_NODE_THREADS: 32, 64, 128 or 256)
@@ -23,9 +35,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_nodes(SimDev s, int par) {
     if (i < s.nn_total) node_step(s, i, par);
 }
 
-cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads,
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads, int group,
                             cudaStream_t st) {
     if (s.nobj == 0) return cudaSuccess;
+    if (group > 1) {  // several objects per block (cluster size and cluster count do not apply)
+        const size_t per = ib_smem_bytes(max_nodes);  // a multiple of 16 bytes
+        const size_t smem = per * (size_t)group;
+        if (group * threads > 1024 || group > 15 || smem > 227 * 1024) return cudaErrorInvalidValue;
+        static SmemAttr gattr;
+        cudaError_t eg = gattr.ensure((const void *)k_membrane_groups, smem, false);
+        if (eg != cudaSuccess) return eg;
+        const int blocks = (s.nobj + group - 1) / group;
+        k_membrane_groups<<<blocks, group * threads, smem, st>>>(s, threads, (int)(per / sizeof(float)));
+        return cudaGetLastError();
+    }
     const size_t smem = ib_smem_bytes(max_nodes);
     static SmemAttr attr;
     cudaError_t ea = attr.ensure((const void *)k_membrane, smem, true);

@@ -125,6 +125,8 @@ __device__ __forceinline__ void corners(const SimDev &s, df x, df y, df z, Corne
     }
 }
 
+namespace cg = cooperative_groups;
+
 __device__ __forceinline__ void mark(uint32_t *mask, int f) { atomicOr(mask + (f >> 5), 1u << (f & 31)); }
 
 // Marks the 4x4x4 lattice nodes (i0-1 .. i0+2, ...) around lower corner
@@ -143,15 +145,45 @@ __device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
     return c;
 }
 
-namespace cg = cooperative_groups;
-
-// Shared memory per block: per node of the largest template the staged
-// position (two float4) and the force (3 floats), plus a small fixed tail.
+// Shared memory per object team: per node of the largest template the
+// staged position (two float4) and the force (3 floats), plus a fixed tail
+// (area / volume partials and factors, the per-warp partial sums of the
+// reductions).  A multiple of 16 bytes, so teams can sit side by side.
 constexpr int IB_SMEM_PER_NODE = 11 * sizeof(float);
-constexpr int IB_SMEM_TAIL = 64;
+constexpr int IB_SMEM_TAIL = 512;
+constexpr int IB_TAIL_WPART = 16;                         // float offset: df [2][IB_THREADS / 32]
+constexpr int IB_TAIL_BOX = IB_TAIL_WPART + 4 * IB_THREADS / 32;  // float [6][IB_THREADS / 32]
+static_assert((IB_TAIL_BOX + 6 * IB_THREADS / 32) * 4 <= IB_SMEM_TAIL, "tail layout");
+
+// The threads that update one object's membrane together: every block of a
+// thread-block cluster (ClusterTeam), or a group of whole warps inside one
+// block (GroupTeam, several objects per block, a named barrier each).
+struct ClusterTeam {
+    cg::cluster_group cl;
+    __device__ __forceinline__ ClusterTeam() : cl(cg::this_cluster()) {}
+    __device__ __forceinline__ int tid() const { return (int)threadIdx.x; }
+    __device__ __forceinline__ int size() const { return (int)blockDim.x; }
+    __device__ __forceinline__ int rank() const { return (int)cl.block_rank(); }
+    __device__ __forceinline__ int ranks() const { return (int)cl.num_blocks(); }
+    __device__ __forceinline__ void sync_block() const { __syncthreads(); }
+    __device__ __forceinline__ void sync_all() const { cl.sync(); }
+    __device__ __forceinline__ float *peer(float *p, int j) const { return cl.map_shared_rank(p, j); }
+};
+struct GroupTeam {
+    int t, n, bar;  // thread index in the group, group size (a multiple of 32), named barrier (1..15)
+    __device__ __forceinline__ int tid() const { return t; }
+    __device__ __forceinline__ int size() const { return n; }
+    __device__ __forceinline__ int rank() const { return 0; }
+    __device__ __forceinline__ int ranks() const { return 1; }
+    __device__ __forceinline__ void sync_block() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+    }
+    __device__ __forceinline__ void sync_all() const { sync_block(); }
+    __device__ __forceinline__ float *peer(float *p, int) const { return p; }
+};
 
 __host__ __device__ inline size_t ib_smem_bytes(int max_nodes) {
-    return (size_t)IB_SMEM_PER_NODE * max_nodes + IB_SMEM_TAIL;
+    return ((size_t)IB_SMEM_PER_NODE * max_nodes + IB_SMEM_TAIL + 15) & ~(size_t)15;
 }
 
 // Sum over a warp of FP32 values as an unevaluated hi + lo pair.
@@ -346,10 +378,12 @@ __device__ __forceinline__ float wall_force(const SimDev &s, float yh, float yl)
 
 // Bounding box of object o from its staged relative positions plus the
 // first node's position (FP32: a broad-phase filter, widened by the
-// cutoff where it is used).  All threads of the block call it.
-__device__ __forceinline__ void object_box(const SimDev &s, int o, const Stage &P, int nn, int f0) {
+// cutoff where it is used).  Every thread of the team calls it.
+template <class Team>
+__device__ __forceinline__ void object_box(const SimDev &s, int o, const Stage &P, int nn, int f0, float *tail,
+                                           const Team &tm) {
     float mn[3] = {3.0e38f, 3.0e38f, 3.0e38f}, mx[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-    for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+    for (int p = tm.tid(); p < nn; p += tm.size()) {
         const float4 h = P.hi[p];
         mn[0] = fminf(mn[0], h.x), mn[1] = fminf(mn[1], h.y), mn[2] = fminf(mn[2], h.z);
         mx[0] = fmaxf(mx[0], h.x), mx[1] = fmaxf(mx[1], h.y), mx[2] = fmaxf(mx[2], h.z);
@@ -361,28 +395,31 @@ __device__ __forceinline__ void object_box(const SimDev &s, int o, const Stage &
             mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], off));
             mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], off));
         }
-    __shared__ float box_part[6][IB_THREADS / 32];
-    if ((threadIdx.x & 31) == 0)
+    float *box_part = tail + IB_TAIL_BOX;  // [6][IB_THREADS / 32]
+    constexpr int W = IB_THREADS / 32;
+    if ((tm.tid() & 31) == 0)
         for (int k = 0; k < 3; ++k) {
-            box_part[k][threadIdx.x >> 5] = mn[k];
-            box_part[3 + k][threadIdx.x >> 5] = mx[k];
+            box_part[k * W + (tm.tid() >> 5)] = mn[k];
+            box_part[(3 + k) * W + (tm.tid() >> 5)] = mx[k];
         }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        const int k = threadIdx.x;
-        float v = box_part[k][0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = k < 3 ? fminf(v, box_part[k][w]) : fmaxf(v, box_part[k][w]);
+    tm.sync_block();
+    if (tm.tid() < 6) {
+        const int k = tm.tid();
+        float v = box_part[k * W];
+        for (int w = 1; w < (tm.size() >> 5); ++w)
+            v = k < 3 ? fminf(v, box_part[k * W + w]) : fmaxf(v, box_part[k * W + w]);
         const int c = k % 3;
         s.aabb[8 * o + k] = v + s.Xh[c * s.nn_total + f0];
     }
 }
 
-// The membrane part of object o by the calling cluster (all C blocks call
-// it): writes the membrane force of each of its nodes to s.Fel (plus the
-// wall repulsion, when set).
-__device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *sh) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+// The membrane part of object o by the calling team (every thread of all
+// its C blocks calls it; sh: the team's shared memory in each block):
+// writes the membrane force of each of its nodes to s.Fel (plus the wall
+// repulsion, when set).
+template <class Team>
+__device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *sh, const Team &tm) {
+    const int C = tm.ranks(), r = tm.rank(), tid = tm.tid(), nthr = tm.size();
     const ObjDev ob = s.obj[o];
     const TplDev &T = s.tpl[ob.tid];
     const int nn = ob.nn, f0 = ob.first, NN = s.nn_total;
@@ -394,7 +431,7 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
     const Forces F{Fx, Fy, Fz};
 
     // 1. stage positions relative to the first node, clear the forces
-    for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+    for (int p = tid; p < nn; p += nthr) {
         df d[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -408,42 +445,43 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
         Fy[p] = 0.f;
         Fz[p] = 0.f;
     }
-    __syncthreads();
+    tm.sync_block();
 
     // 1b. bounding box of the object's nodes (broad phase of the repulsion)
-    if (s.rep_on && r == 0) object_box(s, o, P, nn, f0);
+    if (s.rep_on && r == 0) object_box(s, o, P, nn, f0, tail, tm);
 
     // 2. this block's share of the area and volume sums
     df area{0.f, 0.f}, vol{0.f, 0.f};
     if (T.kag != 0.f || T.kv != 0.f) {
-        for (int t = share_lo(T.nt, r, C) + threadIdx.x; t < share_lo(T.nt, r + 1, C); t += blockDim.x) {
+        for (int t = share_lo(T.nt, r, C) + tid; t < share_lo(T.nt, r + 1, C); t += nthr) {
             const int4 tr = __ldg(T.tri + t);
             const f3 N = cross(P.rel(tr.y, tr.x), P.rel(tr.z, tr.x));
             area = df_add_f(area, 0.5f * sqrtf(dot(N, N)));
             vol = df_add_f(vol, dot(P.pos(tr.x), N));
         }
     }
-    __shared__ df wpart[2][IB_THREADS / 32];
+    df *wpart = (df *)(tail + IB_TAIL_WPART);  // [2][IB_THREADS / 32]
+    constexpr int W = IB_THREADS / 32;
     area = warp_sum_df(area);
     vol = warp_sum_df(vol);
-    if ((threadIdx.x & 31) == 0) {
-        wpart[0][threadIdx.x >> 5] = area;
-        wpart[1][threadIdx.x >> 5] = vol;
+    if ((tid & 31) == 0) {
+        wpart[tid >> 5] = area;
+        wpart[W + (tid >> 5)] = vol;
     }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        df t = wpart[threadIdx.x][0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = df_add(t, wpart[threadIdx.x][w]);
-        tail[2 * threadIdx.x] = t.hi;
-        tail[2 * threadIdx.x + 1] = t.lo;
+    tm.sync_block();
+    if (tid < 2) {
+        df t = wpart[tid * W];
+        for (int w = 1; w < (nthr >> 5); ++w) t = df_add(t, wpart[tid * W + w]);
+        tail[2 * tid] = t.hi;
+        tail[2 * tid + 1] = t.lo;
     }
-    cl.sync();  // staging, cleared forces and partial sums visible in the cluster
+    tm.sync_all();  // staging, cleared forces and partial sums visible to the team
 
     // totals of the object in FP64, partials taken in rank order
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double Sg = 0.0, V6 = 0.0;
         for (int j = 0; j < C; ++j) {
-            const float *pj = cl.map_shared_rank(tail, j);
+            const float *pj = tm.peer(tail, j);
             Sg += (double)pj[0] + (double)pj[1];
             V6 += (double)pj[2] + (double)pj[3];
         }
@@ -452,7 +490,7 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
         tail[4] = (T.kag != 0.f) ? dS / (float)Sg : 0.f;
         tail[5] = (T.kv != 0.f) ? dVol / (float)T.V0 : 0.f;
     }
-    __syncthreads();
+    tm.sync_block();
     const float dSg = tail[4], dV = tail[5];
 
     // 3. this block's share of each kind of element; one loop per kind so
@@ -460,27 +498,27 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
     if (T.ks != 0.f) {
         const int e1 = share_lo32(T.ne, r + 1, C);
 #pragma unroll 2
-        for (int e = share_lo32(T.ne, r, C) + threadIdx.x; e < e1; e += blockDim.x) edge_force(T, P, e, F);
+        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) edge_force(T, P, e, F);
     }
     if (T.kb != 0.f) {
         const int e1 = share_lo32(T.ne, r + 1, C);
 #pragma unroll 2
-        for (int e = share_lo32(T.ne, r, C) + threadIdx.x; e < e1; e += blockDim.x) bending_force(T, P, e, F);
+        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) bending_force(T, P, e, F);
     }
     if (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) {
         const int t1 = share_lo32(T.nt, r + 1, C);
 #pragma unroll 2
-        for (int t = share_lo32(T.nt, r, C) + threadIdx.x; t < t1; t += blockDim.x)
+        for (int t = share_lo32(T.nt, r, C) + tid; t < t1; t += nthr)
             triangle_force(T, P, t, dSg, dV, F);
     }
-    cl.sync();  // every block's partial forces complete
+    tm.sync_all();  // every block's partial forces complete
 
     // 4. this block's share of the nodes: forces summed over the cluster in
     //    rank order
-    for (int p = share_lo(nn, r, C) + threadIdx.x; p < share_lo(nn, r + 1, C); p += blockDim.x) {
+    for (int p = share_lo(nn, r, C) + tid; p < share_lo(nn, r + 1, C); p += nthr) {
         f3 Fp = mk(0.f, 0.f, 0.f);
         for (int j = 0; j < C; ++j) {
-            const float *Fj = cl.map_shared_rank(sh, j) + 8 * nn;
+            const float *Fj = tm.peer(sh, j) + 8 * nn;
             Fp = Fp + mk(Fj[p], Fj[nn + p], Fj[2 * nn + p]);
         }
         if (s.rep_wall_on) Fp.y += wall_force(s, s.Xh[NN + f0 + p], s.Xl[NN + f0 + p]);
@@ -488,7 +526,7 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
         s.Fel[NN + f0 + p] = Fp.y;
         s.Fel[2 * NN + f0 + p] = Fp.z;
     }
-    cl.sync();  // remote reads complete before any block reuses its shared memory
+    tm.sync_all();  // remote reads complete before any block reuses its shared memory
 }
 
 // Coupling part for global node i.

@@ -218,7 +218,8 @@ cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int
 // max_clusters (> 0) looping over the objects (max_nodes sizes shared
 // memory); coupling part: one thread per node
 // threads: block size (a multiple of 32, at most IB_THREADS)
-cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads,
+// group > 1: `group` objects per block of group * threads threads instead
+cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads, int group,
                             cudaStream_t st);
 cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st);
 // object-object repulsion added to Fel (after the membrane kernel, which

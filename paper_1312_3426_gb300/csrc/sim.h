@@ -73,7 +73,8 @@ struct lbib_sim {
     cudaStream_t side = nullptr;
     bool overlap = true;                // membrane of step t+1 on `aux` during fluid of step t
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
-    int membrane_threads = 192;         // block size of the membrane kernel
+    int membrane_threads = 192;         // block size of the membrane kernel (per object)
+    int membrane_group = 1;             // objects per block of the membrane kernel
     int node_threads = lbib::IB_THREADS_DEFAULT;  // nodes per block of the node kernel
 
     double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects

@@ -307,6 +307,7 @@ LBIB_TUNE_MEMBRANE_CLUSTERS = 2
 LBIB_TUNE_MEMBRANE_THREADS = 3
 LBIB_TUNE_FLUID_KERNEL = 4
 LBIB_TUNE_NODE_THREADS = 5
+LBIB_TUNE_MEMBRANE_GROUP = 6
 
 
 def lbib_set_tuning(h, key, value):

@@ -5,16 +5,17 @@ floating-point atomics, only the speed:
 
 * ``LBIB_TUNE_IB_CLUSTER``      thread blocks per object of the membrane kernel;
 * ``LBIB_TUNE_OVERLAP``         membrane kernel beside the fluid kernel (second stream);
-* ``LBIB_TUNE_MEMBRANE_THREADS`` block size of the membrane kernel;
+* ``LBIB_TUNE_MEMBRANE_THREADS`` threads per object of the membrane kernel;
+* ``LBIB_TUNE_MEMBRANE_GROUP``  objects per block of the membrane kernel (single simulations);
 * ``LBIB_TUNE_NODE_THREADS``    nodes per block of the node kernel (the node chunk);
 * ``LBIB_TUNE_FLUID_KERNEL``    16-bit storage: two cells per thread (1), the
   warp-specialised two-cells kernel (2, single simulations only) or one
   cell per thread (3).
 
 ``autotune`` times a few steps of the caller's own simulations for each
-candidate and keeps the fastest, one knob group at a time (membrane shape
-first, then the node chunk, then the fluid kernel, each group searched with
-the best choice of the groups before it).  Results are cached by a key of
+candidate and keeps the fastest, one knob group at a time (membrane shape,
+then objects per membrane block, then the node chunk, then the fluid
+kernel, each group searched with the best choice of the groups before it).  Results are cached by a key of
 the workload's shape (number of simulations, box-size class, node-count
 class, storage precisions, batched or not), so simulations of the same class
 reuse the choice.  Tuning advances the simulations it times; callers tune on
@@ -29,9 +30,10 @@ from . import lbib
 _CACHE: dict = {}
 
 KNOBS = (("cluster", lbib.LBIB_TUNE_IB_CLUSTER), ("overlap", lbib.LBIB_TUNE_OVERLAP),
-         ("membrane_threads", lbib.LBIB_TUNE_MEMBRANE_THREADS), ("node_threads", lbib.LBIB_TUNE_NODE_THREADS),
-         ("fluid_kernel", lbib.LBIB_TUNE_FLUID_KERNEL))
-DEFAULT = {"cluster": 1, "overlap": 1, "membrane_threads": 192, "node_threads": 256, "fluid_kernel": 0}
+         ("membrane_threads", lbib.LBIB_TUNE_MEMBRANE_THREADS), ("membrane_group", lbib.LBIB_TUNE_MEMBRANE_GROUP),
+         ("node_threads", lbib.LBIB_TUNE_NODE_THREADS), ("fluid_kernel", lbib.LBIB_TUNE_FLUID_KERNEL))
+DEFAULT = {"cluster": 1, "overlap": 1, "membrane_threads": 192, "membrane_group": 1, "node_threads": 256,
+           "fluid_kernel": 0}
 
 
 def _key(sims, batched):
@@ -69,13 +71,16 @@ def apply(sims, choice):
             lbib.lbib_set_tuning(s.h, key, int(choice[name]))
 
 
-def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), node_threads=(64, 128, 256)):
+def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), member_groups=(1, 2, 3),
+               node_threads=(64, 128, 256)):
     """The knob groups searched, in order: [(name, ...), [values, ...]]."""
     groups = []
     has_objects = any(int(s.info()[1]) > 0 for s in sims)
     if has_objects:
         groups.append((("cluster", "overlap", "membrane_threads"),
                        [(c, o, t) for c in clusters for o in overlaps for t in threads]))
+        if not batched:  # the batched step keeps one object per block
+            groups.append((("membrane_group",), [(g,) for g in member_groups]))
         groups.append((("node_threads",), [(t,) for t in node_threads]))
     if any(int(s.info()[6]) != lbib.LBIB_POP_F32 for s in sims):
         kernels = (1, 3) if batched else (1, 2, 3)

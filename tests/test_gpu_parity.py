@@ -788,3 +788,25 @@ def test_one_cell_per_thread_knob_for_16_bit_storage(prec, bound):
     lbib.lbib_set_tuning(h.h, lbib.LBIB_TUNE_FLUID_KERNEL, 3)
     lbib.lbib_batch_step([h.h], 300)
     assert rel_l2(h.velocity(), o.velocity(), sc) <= bound
+
+
+@pytest.mark.parametrize("group,threads", [(3, 192), (4, 256), (2, 64)])
+def test_membrane_objects_per_block_knob(group, threads):
+    """Several objects per membrane block (LBIB_TUNE_MEMBRANE_GROUP) give
+    the forces of one object per block, up to the order of the FP32
+    shared-memory atomics; the run matches the oracle."""
+    sc = _two_object_scene(True)
+    sc.objects.append(scenes.Obj(0, (22.0, 9.3, 13.0), (0.4, 0.1, 0.2)))
+    sc.objects.append(scenes.Obj(1, (6.0, 9.0, 22.0), (0.2, 0.3, 0.1)))
+    o = oracle.Oracle.from_scene(sc)
+    o.step(200)
+    g = lbib.Sim.from_scene(sc)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, group)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, threads)
+    assert lbib.lbib_get_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_GROUP) == group
+    g.step(200)
+    g.sync()
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= 1e-5
+    assert nodes_maxabs(g, o, 4) <= NODE_BAR
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, 0)
