@@ -398,7 +398,9 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * LBIB_TUNE_MEMBRANE_THREADS threads of a block of group x threads threads
  * (at most 1024) and the cluster knobs do not apply; the step fails with
  * LBIB_ERR_CUDA when the block does not fit (threads or shared memory).
- * lbib_batch_step ignores it.  Results do not depend on the knobs beyond the order of
+ * lbib_batch_step takes the first simulation's, and keeps one object per
+ * block when the objects' shared memory (sized for the largest) or the
+ * threads do not fit.  Results do not depend on the knobs beyond the order of
  * floating-point atomics (the three 16-bit kernels give identical
  * populations).  LBIB_ERR_ARG for an unknown key or an out-of-range value. */
 typedef enum {

@@ -93,6 +93,19 @@ __global__ void __launch_bounds__(IB_THREADS, 4)
     membrane_object(sims[it.x], it.y, batch_smem, ClusterTeam());
 }
 
+// Several (simulation, object) items per block: group g of block b takes
+// item b G + g with its own shared memory and named barrier g + 1.
+__global__ void __launch_bounds__(1024, 1)
+    k_batch_membrane_groups(const SimDev *__restrict__ sims, const int2 *__restrict__ items, int n_items, int T,
+                            int group_floats) {
+    const int g = (int)threadIdx.x / T, G = (int)blockDim.x / T;
+    const int k = (int)blockIdx.x * G + g;
+    if (k >= n_items) return;  // whole groups only
+    const int2 it = items[k];
+    const GroupTeam tm{(int)threadIdx.x - g * T, T, g + 1};
+    membrane_object(sims[it.x], it.y, batch_smem + (size_t)g * group_floats, tm);
+}
+
 __global__ void k_batch_advance(long long *t_base, int n, int steps) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) t_base[i] += steps;
@@ -106,7 +119,7 @@ struct BatchPlan {
     std::vector<uint64_t> serial;  // identity of each simulation (addresses can be reused)
     std::vector<int> nobj, nn, group;  // group: fluid kernel variant (2 * precision + BC)
     std::vector<SimDev> dev;  // descriptors the device copy holds
-    int cluster = 0, device = -1, mthreads = IB_THREADS, nthreads = IB_THREADS_DEFAULT;
+    int cluster = 0, device = -1, mthreads = IB_THREADS, nthreads = IB_THREADS_DEFAULT, mgroup = 1;
     SimDev *d_sims = nullptr;
     long long *d_t = nullptr;
     int2 *d_items = nullptr;  // fluid (by storage type x obstacles), then node, then membrane items
@@ -253,6 +266,20 @@ static cudaError_t launch_repulsion_batch(cudaStream_t st) {
 
 static cudaError_t launch_membrane_batch(cudaStream_t st) {
     if (g_plan.n_mb == 0) return cudaSuccess;
+    const size_t per = ib_smem_bytes(g_plan.max_nodes);
+    const int G = g_plan.mgroup;
+    if (G > 1 && G * g_plan.mthreads <= 1024 && per * G <= (size_t)227 * 1024) {
+        // several objects per block (the shared-memory slice of each is sized for the largest object)
+        static SmemAttr gattr;
+        cudaError_t e = gattr.ensure((const void *)k_batch_membrane_groups, per * G, false);
+        if (e != cudaSuccess) return e;
+        const int blocks = (g_plan.n_mb + G - 1) / G;
+        k_batch_membrane_groups<<<blocks, G * g_plan.mthreads, per * G, st>>>(
+            (const SimDev *)g_plan.d_sims, (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd), g_plan.n_mb,
+            g_plan.mthreads, (int)(per / sizeof(float)));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return launch_repulsion_batch(st);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(g_plan.n_mb * g_plan.cluster));
     cfg.blockDim = dim3((unsigned)g_plan.mthreads);
@@ -371,8 +398,9 @@ extern "C" lbib_status lbib_batch_step(lbib_sim *const *sims, int n, int n_steps
     cudaError_t e = cudaSuccess;
     const int cluster = sims[0]->cluster;
     if (!plan_matches(sims, n, cluster)) e = build_plan(sims, n, cluster, st);
-    if (g_plan.mthreads != sims[0]->membrane_threads) {
+    if (g_plan.mthreads != sims[0]->membrane_threads || g_plan.mgroup != sims[0]->membrane_group) {
         g_plan.mthreads = sims[0]->membrane_threads;  // captured in the graph
+        g_plan.mgroup = sims[0]->membrane_group;
         g_plan.release_graph();
     }
     // descriptors (node arrays may have been reallocated, tables uploaded)

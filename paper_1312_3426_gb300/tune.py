@@ -6,7 +6,7 @@ floating-point atomics, only the speed:
 * ``LBIB_TUNE_IB_CLUSTER``      thread blocks per object of the membrane kernel;
 * ``LBIB_TUNE_OVERLAP``         membrane kernel beside the fluid kernel (second stream);
 * ``LBIB_TUNE_MEMBRANE_THREADS`` threads per object of the membrane kernel;
-* ``LBIB_TUNE_MEMBRANE_GROUP``  objects per block of the membrane kernel (single simulations);
+* ``LBIB_TUNE_MEMBRANE_GROUP``  objects per block of the membrane kernel;
 * ``LBIB_TUNE_NODE_THREADS``    nodes per block of the node kernel (the node chunk);
 * ``LBIB_TUNE_FLUID_KERNEL``    16-bit storage: two cells per thread (1), the
   warp-specialised two-cells kernel (2, single simulations only) or one
@@ -79,8 +79,7 @@ def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 25
     if has_objects:
         groups.append((("cluster", "overlap", "membrane_threads"),
                        [(c, o, t) for c in clusters for o in overlaps for t in threads]))
-        if not batched:  # the batched step keeps one object per block
-            groups.append((("membrane_group",), [(g,) for g in member_groups]))
+        groups.append((("membrane_group",), [(g,) for g in member_groups]))
         groups.append((("node_threads",), [(t,) for t in node_threads]))
     if any(int(s.info()[6]) != lbib.LBIB_POP_F32 for s in sims):
         kernels = (1, 3) if batched else (1, 2, 3)

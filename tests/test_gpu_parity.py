@@ -810,3 +810,35 @@ def test_membrane_objects_per_block_knob(group, threads):
     assert nodes_maxabs(g, o, 4) <= NODE_BAR
     with pytest.raises(lbib.LbibError):
         lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, 0)
+
+
+@pytest.mark.parametrize("group", [2, 3])
+def test_batched_membrane_objects_per_block_equals_individual_steps(group):
+    """The batched step with several (simulation, object) items per
+    membrane block, items of different simulations sharing a block, gives
+    the individual steps up to the order of the FP32 atomics.  With a
+    level-4 object (2562 nodes, 113 KB of shared memory a slice) two slices
+    fill the block's 227 KB and three do not fit: that batch keeps one
+    object per block."""
+    two = _two_object_scene(True, nx=37, ny=19, nz=29)
+    two.objects.append(scenes.Obj(0, (22.0, 9.3, 13.0), (0.4, 0.1, 0.2)))
+    for scs in ([two, scenes.channel_sphere(with_object=True), _two_object_scene(True)],
+                [_large_object_scene(), two]):
+        alone = [lbib.Sim.from_scene(s) for s in scs]
+        mixed = [lbib.Sim.from_scene(s) for s in scs]
+        for a in alone:
+            a.step(60)
+        lbib.lbib_set_tuning(mixed[0].h, lbib.LBIB_TUNE_MEMBRANE_GROUP, group)
+        lbib.lbib_batch_step([m.h for m in mixed], 30)
+        lbib.lbib_set_tuning(mixed[0].h, lbib.LBIB_TUNE_MEMBRANE_GROUP, 1)  # the graph is rebuilt
+        lbib.lbib_batch_step([m.h for m in mixed], 10)
+        lbib.lbib_set_tuning(mixed[0].h, lbib.LBIB_TUNE_MEMBRANE_GROUP, group)
+        lbib.lbib_batch_step([m.h for m in mixed], 20)
+        for a, m in zip(alone, mixed):
+            ua, um = a.velocity(), m.velocity()
+            assert np.abs(ua - um).max() <= 1e-5 * max(1e-12, np.abs(ua).max())
+            xa, _ = a.read_nodes(-1)
+            xm, _ = m.read_nodes(-1)
+            assert np.abs(xa - xm).max() <= 1e-6
+        for x in alone + mixed:
+            x.close()
