@@ -135,6 +135,32 @@ __device__ __forceinline__ void mark_halo(const SimDev &s, int ix, int iy, int i
     for_each_halo(s, ix, iy, iz, [&](int f) { mark(s.amask, f); });
 }
 
+// mark_halo for the lanes of the calling converged threads that pass
+// `need`: the threads take each such lane's 64 halo nodes together (one
+// or a few nodes per thread), instead of one lane walking 64 nodes while
+// the others of its warp wait.
+__device__ __forceinline__ void mark_halo_coalesced(const SimDev &s, bool need, int3 lc) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned m = g.ballot(need);
+    const int n = (int)g.size(), r = (int)g.thread_rank();
+    while (m) {
+        const int src = __ffs(m) - 1;  // rank in g
+        m &= m - 1;
+        const int ix = g.shfl(lc.x, src), iy = g.shfl(lc.y, src), iz = g.shfl(lc.z, src);
+        for (int j = r; j < 64; j += n) {
+            const int f = halo_cell(s, ix, iy, iz, j);
+            if (f >= 0) mark(s.amask, f);
+        }
+    }
+}
+
+// G[f] += (x, y, z, 0) as one vector reduction: no value comes back, so
+// nothing waits for it.
+__device__ __forceinline__ void red_add_v4(float4 *p, float x, float y, float z) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.f)
+                 : "memory");
+}
+
 // Lower lattice corner of a position.
 __device__ __forceinline__ int3 lower_corner(df x, df y, df z) {
     int3 c;
@@ -313,7 +339,7 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     for (int k = 0; k < 8; ++k) {
         const float w = c.w[k];
         if (c.f[k] >= 0) {
-            atomicAdd(G + c.f[k], make_float4(-w * fdx, -w * fdy, -w * fdz, 0.f));
+            red_add_v4(G + c.f[k], -w * fdx, -w * fdy, -w * fdz);
         } else {
             dropx -= w * fdx;
             dropy -= w * fdy;
@@ -344,12 +370,10 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     Xl[NN + i] = y.lo;
     Xh[2 * NN + i] = z.hi;
     Xl[2 * NN + i] = z.lo;
-    if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) {
-        atomicOr(s.status, ST_NODE_NAN);
-    } else {
-        const int3 lc = lower_corner(x, y, z);
-        if (lc.x != c0.x || lc.y != c0.y || lc.z != c0.z) mark_halo(s, lc.x, lc.y, lc.z);
-    }
+    const bool fin = isfinite(x.hi) && isfinite(y.hi) && isfinite(z.hi);
+    if (!fin) atomicOr(s.status, ST_NODE_NAN);
+    const int3 lc = lower_corner(x, y, z);
+    mark_halo_coalesced(s, fin && (lc.x != c0.x || lc.y != c0.y || lc.z != c0.z), lc);
 }
 
 // Share [r n / C, (r+1) n / C) of n items for cluster rank r.

@@ -13,6 +13,7 @@
 //                   offsets d used below never overflows
 //   corner_cells    every f[k] is -1 or in [0, nx nyf nz)
 //   for_each_halo   calls fn(f) only with f in [0, nx nyf nz)
+//   halo_cell       -1 or in [0, nx nyf nz)
 #pragma once
 
 #include <math.h>
@@ -102,6 +103,14 @@ LBIB_HD void corner_cells(const D &g, float xh, float xl, float yh, float yl, fl
         f[k] = (dy ? in1 : in0) ? (dx ? cx1 : cx0) + g.nx * ((dy ? cy1 : cy0) + g.nyf * (dz ? cz1 : cz0)) : -1;
         w[k] = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
     }
+}
+
+// Fluid index of halo node j in [0, 64) of lower corner (ix, iy, iz):
+// offsets dx = j % 4 - 1, dy = (j / 4) % 4 - 1, dz = j / 16 - 1, so that the
+// 64 values of j give the nodes for_each_halo visits; -1 on a solid row.
+template <class D>
+LBIB_HD int halo_cell(const D &g, int ix, int iy, int iz, int j) {
+    return fluid_index(g, wrapi(ix + (j & 3) - 1, g.nx), iy + ((j >> 2) & 3) - 1, wrapi(iz + (j >> 4) - 1, g.nz));
 }
 
 // Calls fn(f) for every fluid cell of the 4x4x4 lattice nodes

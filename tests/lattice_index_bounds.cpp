@@ -53,12 +53,26 @@ int main(int argc, char **argv) {
         lbib::lattice_coord(r[0], r[1], ix, t);
         lbib::lattice_coord(r[2], r[3], iy, t);
         lbib::lattice_coord(r[4], r[5], iz, t);
+        int seq[64], ns = 0;
         lbib::for_each_halo(g, ix, iy, iz, [&](int c) {
             ++halo_refs;
             if (c < 0 || c >= nf || (c >> 5) >= nwords) ++bad;
             if (c > max_f) max_f = c;
             if ((c >> 5) > max_w) max_w = c >> 5;
+            if (ns < 64) seq[ns] = c;
+            ++ns;
         });
+        // halo_cell over j = 0..63 gives the same cells in the same order
+        int nj = 0;
+        for (int j = 0; j < 64; ++j) {
+            const int c = lbib::halo_cell(g, ix, iy, iz, j);
+            if (c < -1 || c >= nf) ++bad;
+            if (c >= 0) {
+                if (nj >= ns || seq[nj] != c) ++bad;
+                ++nj;
+            }
+        }
+        if (nj != ns || ns > 64) ++bad;
     }
     std::printf("%lld %lld %lld %lld %lld %lld %lld %lld %lld\n", nodes, skipped, corner_refs, halo_refs, bad, max_f,
                 max_w, nf, nwords);
