@@ -472,28 +472,27 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
         std::memcpy(&i, &f, 4);
         return i;
     };
-    std::vector<int32_t> tri4(4 * (size_t)nt), edge4(4 * (size_t)T.ne), quad4(4 * (size_t)T.ne);
-    std::vector<float> ith0(T.ne);
+    std::vector<int32_t> tri4(4 * (size_t)nt), quad4(4 * (size_t)T.ne);
+    std::vector<float> hinge4(4 * (size_t)T.ne);
     // device records in the conflict-free evaluation order of each kind
     for (int j = 0; j < nt; ++j) {
         const int t = T.tri_order[j];
         for (int k = 0; k < 3; ++k) tri4[4 * j + k] = T.tri[3 * t + k];
         tri4[4 * j + 3] = fbits(T.S0[t]);
     }
+    // edge e is (b, c) of bending quad e = (a, b, c, d): one record per edge
+    // carries both (the stretching and the bending of that edge)
     for (int j = 0; j < T.ne; ++j) {
-        const int e = T.edge_order[j];
-        edge4[4 * j] = T.edges[2 * e];
-        edge4[4 * j + 1] = T.edges[2 * e + 1];
-        edge4[4 * j + 2] = fbits(T.L0[e]);
-        edge4[4 * j + 3] = fbits(1.0 / T.L0[e]);
-        const int q = T.quad_order[j];
-        for (int k = 0; k < 4; ++k) quad4[4 * j + k] = T.quads[4 * q + k];
-        ith0[j] = (float)(1.0 / T.theta0[q]);
+        const int e = T.quad_order[j];
+        for (int k = 0; k < 4; ++k) quad4[4 * j + k] = T.quads[4 * e + k];
+        hinge4[4 * j] = (float)T.L0[e];
+        hinge4[4 * j + 1] = (float)(1.0 / T.L0[e]);
+        hinge4[4 * j + 2] = (float)(1.0 / T.theta0[e]);
+        hinge4[4 * j + 3] = 0.f;
     }
     const size_t o_tri = put(tri4.data(), tri4.size() * 4);
-    const size_t o_edge = put(edge4.data(), edge4.size() * 4);
     const size_t o_quad = put(quad4.data(), quad4.size() * 4);
-    const size_t o_ith0 = put(ith0.data(), ith0.size() * 4);
+    const size_t o_hinge = put(hinge4.data(), hinge4.size() * 4);
     cudaError_t e = cudaMemcpyAsync(mem, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -514,9 +513,8 @@ lbib_status lbib_template_create(lbib_sim *s, int tid, const double *xyz, int nn
     dv.V0 = T.V0;
     dv.ne = T.ne;
     dv.tri = (const int4 *)(b + o_tri);
-    dv.edge = (const int4 *)(b + o_edge);
     dv.quad = (const int4 *)(b + o_quad);
-    dv.inv_theta0 = (const float *)(b + o_ith0);
+    dv.hinge = (const float4 *)(b + o_hinge);
     s->topo.push_back(std::move(T));
     s->tpl_dev.push_back(dv);
     s->tpl_mem.push_back(mem);

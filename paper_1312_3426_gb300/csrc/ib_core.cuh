@@ -231,43 +231,50 @@ struct Forces {
     }
 };
 
-__device__ __forceinline__ void edge_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
-    const int4 r = __ldg(T.edge + e);  // (a, b, L0 bits, 1/L0 bits)
-    const float L0 = __int_as_float(r.z), iL0 = __int_as_float(r.w);
-    const f3 d = P.rel(r.y, r.x);
-    const float il = rsqrtf(dot(d, d));
-    const float L = dot(d, d) * il;
-    const float lam = L * iL0;
-    float kap = 1.f;
-    if (T.nonlinear) {  // (lambda^0.5 + lambda^-2.5) / (lambda + lambda^-3)
-        // lambda stays near 1: the fast reciprocal and quotient are within 2 ulp
-        const float sl = sqrtf(lam), il3 = __fdividef(1.f, lam * lam * lam);
-        kap = __fdividef(sl + il3 * sl, lam + il3);
+// The two forces that live on edge e = (b, c) of the hinge (a, b, c, d)
+// (triangles (a, b, c) and (d, c, b)): the stretching of the edge and the
+// bending between the two triangles.  One pass over the edges serves both:
+// they share the record, the staged positions of b and c and the vector
+// c - b, and their forces on b and c are summed before the shared-memory
+// reductions (the order of FP32 additions into a node is not fixed anyway).
+__device__ __forceinline__ void hinge_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
+    const int4 q = __ldg(T.quad + e);
+    const float4 h = __ldg(T.hinge + e);  // (L0, 1/L0, 1/theta0, 0)
+    const f3 C = P.rel(q.z, q.y);         // c - b
+    f3 fb = mk(0.f, 0.f, 0.f), fc = fb;
+    if (T.ks != 0.f) {  // stretching along c - b
+        const float il = rsqrtf(dot(C, C));
+        const float L = dot(C, C) * il;
+        const float lam = L * h.y;
+        float kap = 1.f;
+        if (T.nonlinear) {  // (lambda^0.5 + lambda^-2.5) / (lambda + lambda^-3)
+            // lambda stays near 1: the fast reciprocal and quotient are within 2 ulp
+            const float sl = sqrtf(lam), il3 = __fdividef(1.f, lam * lam * lam);
+            kap = __fdividef(sl + il3 * sl, lam + il3);
+        }
+        fb = (T.ks * kap * (L - h.x) * h.y * il) * C;
+        fc = -1.f * fb;
     }
-    const f3 f = (T.ks * kap * (L - L0) * iL0 * il) * d;
-    F.add(r.x, f);
-    F.add(r.y, -1.f * f);
-}
-
-__device__ __forceinline__ void bending_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
-    const int4 q = __ldg(T.quad + e);  // (a, b, c, d): triangles (a,b,c) and (d,c,b)
-    const float ith0 = __ldg(T.inv_theta0 + e);
-    const f3 A = P.rel(q.x, q.y), C = P.rel(q.z, q.y), D = P.rel(q.w, q.y);  // relative to b
-    f3 n1 = cross(-1.f * A, C - A);  // (b-a) x (c-a)
-    f3 n2 = cross(C - D, -1.f * D);  // (c-d) x (b-d)
-    n1 = rsqrtf(dot(n1, n1)) * n1;
-    n2 = rsqrtf(dot(n2, n2)) * n2;
-    const f3 cr = cross(n1, n2);
-    const float alpha = atan2f(sqrtf(dot(cr, cr)), dot(n1, n2));
-    const float PI_F = 3.14159265358979f;
-    const float theta = dot(D, n1) > 0.f ? PI_F - alpha : PI_F + alpha;
-    const float sb = T.kb * (theta * ith0 - 1.f);
-    const f3 fa = sb * n1, fd = sb * n2;
-    const f3 fe = -0.5f * (fa + fd);
-    F.add(q.x, fa);
-    F.add(q.w, fd);
-    F.add(q.y, fe);
-    F.add(q.z, fe);
+    if (T.kb != 0.f) {  // bending: the angle between the two triangles' normals
+        const f3 A = P.rel(q.x, q.y), D = P.rel(q.w, q.y);  // relative to b
+        f3 n1 = cross(-1.f * A, C - A);  // (b-a) x (c-a)
+        f3 n2 = cross(C - D, -1.f * D);  // (c-d) x (b-d)
+        n1 = rsqrtf(dot(n1, n1)) * n1;
+        n2 = rsqrtf(dot(n2, n2)) * n2;
+        const f3 cr = cross(n1, n2);
+        const float alpha = atan2f(sqrtf(dot(cr, cr)), dot(n1, n2));
+        const float PI_F = 3.14159265358979f;
+        const float theta = dot(D, n1) > 0.f ? PI_F - alpha : PI_F + alpha;
+        const float sb = T.kb * (theta * h.z - 1.f);
+        const f3 fa = sb * n1, fd = sb * n2;
+        const f3 fe = -0.5f * (fa + fd);
+        F.add(q.x, fa);
+        F.add(q.w, fd);
+        fb = fb + fe;
+        fc = fc + fe;
+    }
+    F.add(q.y, fb);
+    F.add(q.z, fc);
 }
 
 __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, int t, float dSg, float dV,
@@ -519,15 +526,10 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
 
     // 3. this block's share of each kind of element; one loop per kind so
     //    that independent iterations overlap
-    if (T.ks != 0.f) {
+    if (T.ks != 0.f || T.kb != 0.f) {
         const int e1 = share_lo32(T.ne, r + 1, C);
 #pragma unroll 2
-        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) edge_force(T, P, e, F);
-    }
-    if (T.kb != 0.f) {
-        const int e1 = share_lo32(T.ne, r + 1, C);
-#pragma unroll 2
-        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) bending_force(T, P, e, F);
+        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) hinge_force(T, P, e, F);
     }
     if (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) {
         const int t1 = share_lo32(T.nt, r + 1, C);

@@ -85,9 +85,10 @@ struct TplDev {
     int kal_altitude;  // local-area force along the altitudes (else centroid -> vertex)
     double Sg0, V0;
     const int4 *tri;
-    const int4 *edge;
+    // per edge (b, c) with its two triangles (a, b, c) and (d, c, b): the
+    // nodes (a, b, c, d) and (L0, 1/L0, 1/theta0, 0), in one order
     const int4 *quad;
-    const float *inv_theta0;
+    const float4 *hinge;
 };
 
 // One object: its template, first global node, node count and 1/m.

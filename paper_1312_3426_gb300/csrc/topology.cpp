@@ -159,7 +159,6 @@ bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, cons
         return false;
     }
 
-    T.edge_order = conflict_free_order(T.edges, 2, 32);
     T.quad_order = conflict_free_order(T.quads, 4, 32);
     T.tri_order = conflict_free_order(T.tri, 3, 32);
     return true;

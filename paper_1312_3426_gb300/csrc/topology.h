@@ -13,13 +13,14 @@ struct Topology {
     std::vector<double> x;                    // stretched rest coordinates [nn][3]
     std::vector<int> tri;                     // [nt][3] as given
     std::vector<int> edges;                   // [ne][2], i < j, lexicographic
-    std::vector<int> quads;                   // [ne][4] (a, b, c, d)
+    std::vector<int> quads;                   // [ne][4] (a, b, c, d); edge e is (b, c) of quad e
     std::vector<double> L0, theta0, S0;       // [ne], [ne], [nt]
     double Sg0 = 0.0, V0 = 0.0;
-    // device evaluation order of each element list: consecutive groups of 32
-    // elements touch pairwise-different nodes where possible, so the lanes of
-    // a warp add to different nodes' force sums
-    std::vector<int> edge_order, quad_order, tri_order;
+    // device evaluation order of each element list (edges go with their
+    // quads): consecutive groups of 32 elements touch pairwise-different
+    // nodes where possible, so the lanes of a warp add to different nodes'
+    // force sums
+    std::vector<int> quad_order, tri_order;
 };
 
 // Greedy packing of elements (node lists of `arity` ids each) into groups of

@@ -59,6 +59,9 @@ def test_topology_bit_exact_against_oracle(name, nt, stretch):
     ref = o.topology(0, len(tris))
     assert np.array_equal(lib["edges"], ref["edges"])
     assert np.array_equal(lib["quads"], ref["quads"])
+    # the device's per-edge record holds edge e's stretching and bending:
+    # edge e must be the middle pair (b, c) of quad e
+    assert np.array_equal(lib["quads"][:, 1:3], lib["edges"])
     assert np.allclose(lib["L0"], ref["L0"], rtol=1e-14, atol=0)
     assert np.allclose(lib["theta0"], ref["theta0"], rtol=1e-13, atol=0)
     assert np.allclose(lib["S0"], ref["S0"], rtol=1e-13, atol=0)
