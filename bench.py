@@ -295,16 +295,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def apply_knobs(args, lbib, sim):
+    """The launch-shape knobs given on the command line."""
+    if args.ib_cluster:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
+    if args.overlap >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
+    if args.membrane_clusters >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
+    if args.fluid_kernel >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_FLUID_KERNEL, args.fluid_kernel)
+    if args.membrane_threads:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, args.membrane_threads)
+    if args.node_threads:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_NODE_THREADS, args.node_threads)
+    if args.membrane_group:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, args.membrane_group)
+
+
+def explicit_knobs(args):
+    return bool(args.ib_cluster or args.overlap >= 0 or args.membrane_clusters >= 0 or args.fluid_kernel >= 0
+                or args.membrane_threads or args.node_threads or args.membrane_group)
+
+
 def batch_workload(args, lbib, torch, dev, stream):
     """64 independent channels (random boxes 32^3..128x64x64, 0-40 cells of
     level 2/3/4, FP32) advanced together by lbib_batch_step; knobs from the
-    autotuner.  Returns the fields of the JSON line."""
+    autotuner, or from the command line (then on every simulation; the batch
+    takes the first one's).  Returns the fields of the JSON line."""
     from paper_1312_3426_gb300 import tune
     from workloads import scenes
     scs = scenes.batch_mix(64)
     sims = [lbib.Sim.from_scene(sc, precision=args.precision, pop_scale_log2=args.scale_log2,
                                 stream=stream.cuda_stream) for sc in scs]
-    choice, timing = tune.autotune(sims, steps=32, batched=True)
+    for s in sims:
+        apply_knobs(args, lbib, s)
+    tuning = None
+    if not args.no_autotune and not explicit_knobs(args):
+        choice, timing = tune.autotune(sims, steps=32, batched=True)
+        tuning = dict(choice, candidates_s={k: round(v, 5) for k, v in timing.items()})
     h = [s.h for s in sims]
     lbib.lbib_batch_step(h, max(3, args.warmup))
     torch.cuda.synchronize()
@@ -326,7 +355,7 @@ def batch_workload(args, lbib, torch, dev, stream):
     nodes = sum(sc.n_nodes for sc in scs)
     for s in sims:
         s.close()
-    return scs, cells, nodes, ms, clocks, dict(choice, candidates_s={k: round(v, 5) for k, v in timing.items()})
+    return scs, cells, nodes, ms, clocks, tuning
 
 
 def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier, e2e=True, launch="separate",
@@ -339,24 +368,9 @@ def measure(args, lbib, torch, sc, precision, stream, dev, local, world, barrier
     loop of e2e_record.  Returns the numbers of the JSON line."""
     sim = lbib.Sim.from_scene(sc, precision=precision, pop_scale_log2=args.scale_log2, stream=stream.cuda_stream)
     nf = sc.n_fluid_cells
-    if args.ib_cluster:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_IB_CLUSTER, args.ib_cluster)
-    if args.overlap >= 0:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_OVERLAP, args.overlap)
-    if args.membrane_clusters >= 0:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_CLUSTERS, args.membrane_clusters)
-    if args.fluid_kernel >= 0:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_FLUID_KERNEL, args.fluid_kernel)
-    if args.membrane_threads:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_THREADS, args.membrane_threads)
-    if args.node_threads:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_NODE_THREADS, args.node_threads)
-    if args.membrane_group:
-        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, args.membrane_group)
+    apply_knobs(args, lbib, sim)
     tuning = None
-    explicit = (args.ib_cluster or args.overlap >= 0 or args.membrane_clusters >= 0 or args.fluid_kernel >= 0
-                or args.membrane_threads or args.node_threads or args.membrane_group)
-    if not args.no_autotune and not explicit:
+    if not args.no_autotune and not explicit_knobs(args):
         # the project's autotuner picks the launch shapes on this simulation
         # (it advances it: part of the warm-up)
         from paper_1312_3426_gb300 import tune

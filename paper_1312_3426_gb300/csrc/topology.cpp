@@ -273,31 +273,44 @@ bool orient_mesh(const double *xyz, int nn, const int32_t *tris, int nt, int mod
     return true;
 }
 
-std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width) {
+std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width, int window) {
     const int n = (int)(nodes.size() / arity);
     int max_node = 0;
     for (int v : nodes) max_node = std::max(max_node, v);
-    std::vector<int> stamp(max_node + 1, -1), order, rest;
-    std::vector<int> remaining(n);
+    std::vector<int> stamp(max_node + 1, -1), order, remaining(n);
     for (int i = 0; i < n; ++i) remaining[i] = i;
     order.reserve(n);
-    int group = 0;
-    while (!remaining.empty()) {
-        rest.clear();
-        int filled = 0;
-        for (int e : remaining) {
-            bool free = filled < width;
-            for (int k = 0; k < arity && free; ++k) free = stamp[nodes[arity * e + k]] != group;
-            if (free) {
-                for (int k = 0; k < arity; ++k) stamp[nodes[arity * e + k]] = group;
-                order.push_back(e);
-                ++filled;
-            } else {
-                rest.push_back(e);
+    std::vector<int> res32(32 * arity), res8(8 * arity);
+    constexpr int NODE_TAKEN = 1 << 20;
+    for (int group = 0; !remaining.empty(); ++group) {
+        std::fill(res32.begin(), res32.end(), 0);
+        for (int lane = 0; lane < width && !remaining.empty(); ++lane) {
+            if (lane % 8 == 0) std::fill(res8.begin(), res8.end(), 0);
+            const int scan = std::min((int)remaining.size(), window);
+            int best = 0, best_cost = -1;
+            for (int j = 0; j < scan; ++j) {
+                const int *e = &nodes[(size_t)arity * remaining[j]];
+                int c = 0;
+                for (int k = 0; k < arity; ++k) {
+                    if (stamp[e[k]] == group) c += NODE_TAKEN;
+                    c += 3 * res32[32 * k + (e[k] & 31)] + 2 * res8[8 * k + (e[k] & 7)];
+                }
+                if (best_cost < 0 || c < best_cost) {
+                    best_cost = c;
+                    best = j;
+                    if (c == 0) break;
+                }
             }
+            const int eb = remaining[best];
+            remaining.erase(remaining.begin() + best);
+            const int *e = &nodes[(size_t)arity * eb];
+            for (int k = 0; k < arity; ++k) {
+                stamp[e[k]] = group;
+                ++res32[32 * k + (e[k] & 31)];
+                ++res8[8 * k + (e[k] & 7)];
+            }
+            order.push_back(eb);
         }
-        remaining.swap(rest);
-        ++group;
     }
     return order;
 }

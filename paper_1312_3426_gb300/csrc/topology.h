@@ -23,9 +23,17 @@ struct Topology {
     std::vector<int> quad_order, tri_order;
 };
 
-// Greedy packing of elements (node lists of `arity` ids each) into groups of
-// `width` with disjoint nodes; returns the evaluation order.
-std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width);
+// Evaluation order of elements (node lists of `arity` ids each) for the
+// membrane kernel, whose warps take `width` (32) consecutive elements, one
+// per lane, and for each node slot k load the staged positions (16 bytes per
+// node, 8 lanes per shared-memory wavefront) and add forces (4 bytes per node
+// and component, 32 banks).  Greedy, lane by lane: each lane takes, among the
+// first `window` remaining elements, the first of least cost, where a node
+// already in the group costs most, then each slot's node index sharing its
+// residue mod 32 with an earlier lane of the group (an atomic bank
+// conflict), then mod 8 with an earlier lane of the same quarter (a 16-byte
+// load conflict).
+std::vector<int> conflict_free_order(const std::vector<int> &nodes, int arity, int width, int window = 1024);
 
 bool build_template(const double *xyz, int nn, const int32_t *tris, int nt, const double stretch[3],
                     Topology &out, std::string &err);
