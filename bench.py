@@ -74,6 +74,8 @@ def parse_args():
                     help="block size of the membrane kernel (0: library default)")
     ap.add_argument("--node-threads", type=int, default=0, help="nodes per block of the node kernel (0: default)")
     ap.add_argument("--membrane-group", type=int, default=0, help="objects per membrane block (0: library default)")
+    ap.add_argument("--early-launch", type=int, default=-1, choices=(-1, 0, 1),
+                    help="programmatic dependent launch of the node and fluid kernels (-1: library default)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's launch shapes (and the flags above) instead of autotuning them")
     ap.add_argument("--fluid-kernel", type=int, default=-1, choices=(-1, 0, 1, 2, 3),
@@ -311,11 +313,13 @@ def apply_knobs(args, lbib, sim):
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_NODE_THREADS, args.node_threads)
     if args.membrane_group:
         lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, args.membrane_group)
+    if args.early_launch >= 0:
+        lbib.lbib_set_tuning(sim.h, lbib.LBIB_TUNE_EARLY_LAUNCH, args.early_launch)
 
 
 def explicit_knobs(args):
     return bool(args.ib_cluster or args.overlap >= 0 or args.membrane_clusters >= 0 or args.fluid_kernel >= 0
-                or args.membrane_threads or args.node_threads or args.membrane_group)
+                or args.membrane_threads or args.node_threads or args.membrane_group or args.early_launch >= 0)
 
 
 def batch_workload(args, lbib, torch, dev, stream):

@@ -400,7 +400,12 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * LBIB_ERR_CUDA when the block does not fit (threads or shared memory).
  * lbib_batch_step takes the first simulation's, and keeps one object per
  * block when the objects' shared memory (sized for the largest) or the
- * threads do not fit.  Results do not depend on the knobs beyond the order of
+ * threads do not fit.  LBIB_TUNE_EARLY_LAUNCH: 1 lets each node-update and
+ * fluid kernel of lbib_step after the first start while the kernel before
+ * it finishes (programmatic dependent launch: the early part reads only data
+ * that kernel does not write, and waits for it before the rest), 0 (default)
+ * launches them one after the other; lbib_batch_step ignores it.
+ * Results do not depend on the knobs beyond the order of
  * floating-point atomics (the three 16-bit kernels give identical
  * populations).  LBIB_ERR_ARG for an unknown key or an out-of-range value. */
 typedef enum {
@@ -410,7 +415,8 @@ typedef enum {
     LBIB_TUNE_MEMBRANE_THREADS = 3,
     LBIB_TUNE_FLUID_KERNEL = 4,
     LBIB_TUNE_NODE_THREADS = 5,
-    LBIB_TUNE_MEMBRANE_GROUP = 6
+    LBIB_TUNE_MEMBRANE_GROUP = 6,
+    LBIB_TUNE_EARLY_LAUNCH = 7
 } lbib_tune_key;
 LBIB_API lbib_status lbib_set_tuning(lbib_sim *sim, int key, int value);
 LBIB_API lbib_status lbib_get_tuning(const lbib_sim *sim, int key, int *value);

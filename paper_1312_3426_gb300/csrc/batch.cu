@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(FLUID_THREADS, 5)
     const int2 it = items[blockIdx.x];  // (simulation, block of cells)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
-    fluid_block<T, BC>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
+    fluid_block<T, BC, false>(s, (int)(t & 1), it.y * FLUID_THREADS, step_seed(t));
 }
 
 // 16-bit storage, even nx, plain boundaries: two cells per thread.
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(FLUID_THREADS, 3)
     const SimDev &s = sims[it.x];
     const long long t = t_base[it.x] + step_off;
     const int f = 2 * (it.y * FLUID_THREADS + (int)threadIdx.x);
-    if (f < s.nf) fluid_pair<T>(s, (int)(t & 1), f, step_seed(t));
+    if (f < s.nf) fluid_pair<T, false>(s, (int)(t & 1), f, step_seed(t));
 }
 
 // NT nodes per work item (the plan's node chunk)
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT, 768 / NT)
     const int2 it = items[blockIdx.x];  // (simulation, first node)
     const SimDev &s = sims[it.x];
     const int i = it.y + (int)threadIdx.x;
-    if (i < s.nn_total) node_step(s, i, (int)((t_base[it.x] + step_off) & 1));
+    if (i < s.nn_total) node_step<false>(s, i, (int)((t_base[it.x] + step_off) & 1));
 }
 
 __global__ void __launch_bounds__(IB_THREADS, 4)

@@ -810,7 +810,19 @@ lbib_status lbib_step(lbib_sim *s, int n) {
             if (r != LBIB_OK) return r;
             LBIB_CUDA(s, cudaEventRecord(ev[0], s->stream), "profile event");
         }
-        if (objects) LBIB_CUDA(s, launch_nodes(s->d, par, s->node_threads, s->stream), "node update");
+        // Early launch (programmatic dependent launch), after the first step
+        // of the call and off the sampled steps: the node kernel may start
+        // while the previous fluid kernel (or the mask rebuild or membrane
+        // kernel after it) finishes, reading only node positions,
+        // velocities and object tables before it waits (the previous node
+        // kernel, their only writer, completed before that fluid kernel got
+        // past its own wait); the fluid kernel may start while the node
+        // kernel finishes, pulling populations the previous fluid kernel
+        // wrote (complete once the node kernel got past its wait, and the
+        // node kernel releases only after it) before it waits for the mask
+        // and the coupling buffer.
+        const bool early = s->early_launch && i > 0 && !s->prof_now;
+        if (objects) LBIB_CUDA(s, launch_nodes(s->d, par, s->node_threads, s->stream, early), "node update");
         if (objects && s->overlap) {
             LBIB_CUDA(s, cudaEventRecord(s->ev_nodes, s->stream), "event");
             LBIB_CUDA(s, cudaStreamWaitEvent(s->aux, s->ev_nodes, 0), "event");
@@ -819,7 +831,7 @@ lbib_status lbib_step(lbib_sim *s, int n) {
             LBIB_CUDA(s, cudaEventRecord(s->ev_membrane, s->aux), "event");
         }
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[1], s->stream), "profile event");
-        LBIB_CUDA(s, launch_fluid(s->d, par, (long long)s->t, s->stream), "fluid step");
+        LBIB_CUDA(s, launch_fluid(s->d, par, (long long)s->t, s->stream, early && objects), "fluid step");
         if (ev) LBIB_CUDA(s, cudaEventRecord(ev[2], s->stream), "profile event");
         if (objects && s->overlap) LBIB_CUDA(s, cudaStreamWaitEvent(s->stream, s->ev_membrane, 0), "event");
         s->t++;
@@ -1177,6 +1189,11 @@ lbib_status lbib_set_tuning(lbib_sim *s, int key, int value) {
         s->node_threads = value;
         return LBIB_OK;
     }
+    if (key == LBIB_TUNE_EARLY_LAUNCH) {
+        if (value != 0 && value != 1) return fail(s, LBIB_ERR_ARG, "early launch must be 0 or 1");
+        s->early_launch = value != 0;
+        return LBIB_OK;
+    }
     return fail(s, LBIB_ERR_ARG, "unknown tuning key");
 }
 
@@ -1208,6 +1225,10 @@ lbib_status lbib_get_tuning(const lbib_sim *s, int key, int *value) {
     }
     if (key == LBIB_TUNE_MEMBRANE_GROUP) {
         *value = s->membrane_group;
+        return LBIB_OK;
+    }
+    if (key == LBIB_TUNE_EARLY_LAUNCH) {
+        *value = s->early_launch ? 1 : 0;
         return LBIB_OK;
     }
     return LBIB_ERR_ARG;

@@ -24,21 +24,22 @@
 
 namespace lbib {
 
-template <typename T, bool BC>
+// EARLY: the instantiation for an early (programmatic dependent) launch
+template <typename T, bool BC, bool EARLY>
 __global__ void __launch_bounds__(FLUID_THREADS, 5) k_fluid(SimDev s, int par, uint32_t seed, int pf) {
     prefetch_sources<sizeof(T), FLUID_THREADS>(s, s.pop[par], pf);
-    fluid_block<T, BC>(s, par, blockIdx.x * FLUID_THREADS, seed);
+    fluid_block<T, BC, EARLY>(s, par, blockIdx.x * FLUID_THREADS, seed);
 }
 
 // 16-bit storage, even nx, no obstacles, no inlet: two cells per thread.
 // Blocks of 128 threads (6 per SM at 80 registers): when a membrane block
 // shares the SM, one of six fluid blocks gives way instead of one of three.
 constexpr int PAIR_THREADS = 128;
-template <typename T>
+template <typename T, bool EARLY>
 __global__ void __launch_bounds__(PAIR_THREADS, 6) k_fluid_pair(SimDev s, int par, uint32_t seed, int pf) {
     prefetch_sources<2, 2 * PAIR_THREADS>(s, s.pop[par], pf);
     const int f = 2 * (int)(blockIdx.x * PAIR_THREADS + threadIdx.x);
-    if (f < s.nf) fluid_pair<T>(s, par, f, seed);
+    if (f < s.nf) fluid_pair<T, EARLY>(s, par, f, seed);
 }
 
 static bool pair_shape(const SimDev &s) { return (s.nx & 1) == 0 && !s.solid && !s.in_on; }
@@ -67,36 +68,40 @@ static int device_sms() {
 // Prefetch distances (in blocks), measured at 256x128x128 and 512x256x256
 // on a GB300: 1.5 blocks per SM ahead for the one-cell kernel (5 resident
 // per SM), 3 per SM for the two-cells kernel (6 resident per SM).
+// pdl: the warp-specialised kernel is always launched plainly.
 template <typename T>
-static void launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st) {
+static cudaError_t launch_fluid_t(const SimDev &s, int par, uint32_t seed, int blocks, cudaStream_t st, bool pdl) {
     const int sms = device_sms();
     if constexpr (sizeof(T) == 2) {
         if (fluid_kernel_kind(s) == 2) {
             launch_fluid_tma(s, par, seed, st);
-            return;
+            return cudaGetLastError();
         }
         if (fluid_kernel_kind(s) == 1) {
-            const int pblocks = (s.nf / 2 + PAIR_THREADS - 1) / PAIR_THREADS;
-            k_fluid_pair<T><<<pblocks, PAIR_THREADS, 0, st>>>(s, par, seed, 3 * sms);
-            return;
+            const unsigned pblocks = (unsigned)((s.nf / 2 + PAIR_THREADS - 1) / PAIR_THREADS);
+            if (pdl) return launch_dep(k_fluid_pair<T, true>, pblocks, PAIR_THREADS, st, true, s, par, seed, 3 * sms);
+            return launch_dep(k_fluid_pair<T, false>, pblocks, PAIR_THREADS, st, false, s, par, seed, 3 * sms);
         }
     }
-    if (s.solid || s.in_on)
-        k_fluid<T, true><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed, 3 * sms / 2);
-    else
-        k_fluid<T, false><<<blocks, FLUID_THREADS, 0, st>>>(s, par, seed, 3 * sms / 2);
+    const unsigned b = (unsigned)blocks;
+    const int pf = 3 * sms / 2;
+    if (s.solid || s.in_on) {
+        if (pdl) return launch_dep(k_fluid<T, true, true>, b, FLUID_THREADS, st, true, s, par, seed, pf);
+        return launch_dep(k_fluid<T, true, false>, b, FLUID_THREADS, st, false, s, par, seed, pf);
+    }
+    if (pdl) return launch_dep(k_fluid<T, false, true>, b, FLUID_THREADS, st, true, s, par, seed, pf);
+    return launch_dep(k_fluid<T, false, false>, b, FLUID_THREADS, st, false, s, par, seed, pf);
 }
 
-cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st) {
+cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st, bool pdl) {
     const uint32_t seed = step_seed(t);
     const int blocks = (s.nf + FLUID_THREADS - 1) / FLUID_THREADS;
     switch (s.prec) {
-        case LBIB_POP_F32: launch_fluid_t<float>(s, par, seed, blocks, st); break;
-        case LBIB_POP_F16S: launch_fluid_t<__half>(s, par, seed, blocks, st); break;
-        case LBIB_POP_BF16S: launch_fluid_t<__nv_bfloat16>(s, par, seed, blocks, st); break;
+        case LBIB_POP_F32: return launch_fluid_t<float>(s, par, seed, blocks, st, pdl);
+        case LBIB_POP_F16S: return launch_fluid_t<__half>(s, par, seed, blocks, st, pdl);
+        case LBIB_POP_BF16S: return launch_fluid_t<__nv_bfloat16>(s, par, seed, blocks, st, pdl);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- read-outs

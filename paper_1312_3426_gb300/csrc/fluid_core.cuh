@@ -413,8 +413,19 @@ __device__ __forceinline__ float collide_increment(const SimDev &s, float *__res
 
 // BC: the variant for simulations with obstacles or a velocity inlet (the
 // plain variant carries no test for either).
-template <typename T, bool BC>
-__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, bool active, uint32_t step_seed) {
+// The active-cell word of the warp that owns fluid cell f (blocks start at
+// multiples of 32, so a warp owns exactly one word).  Read through L2: the
+// object update of the same launch may set bits.
+__device__ __forceinline__ uint32_t active_word(const SimDev &s, int f) {
+    const int w = f >> 5;
+    return (w < s.nwords) ? __ldcg(s.amask + w) : 0u;
+}
+
+// EARLY: the kernel may be launched early (programmatic dependent launch):
+// the mask word is read after dep_wait(); otherwise it is `act`, read by the
+// caller before the pulls.
+template <typename T, bool BC, bool EARLY>
+__device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, uint32_t act, uint32_t step_seed) {
     static_assert(d3q19_opp(1) == 2 && d3q19_opp(17) == 18, "directions 2k-1, 2k must be opposite");
     const T *__restrict__ src = (const T *)s.pop[par];
     T *__restrict__ dst = (T *)s.pop[par ^ 1];
@@ -434,6 +445,14 @@ __device__ __forceinline__ void fluid_cell(const SimDev &s, int par, int fi, boo
 #undef LBIB_PULL
 
     if (BC && s.in_on) inlet_cell(s, (int)x, (int)y + s.walls, (int)z, h);
+    // the populations pulled above were written by the previous fluid step;
+    // the mask and the coupling buffer below by the node update of this one
+    if constexpr (EARLY) {
+        dep_wait();
+        dep_release();
+        act = active_word(s, fi);
+    }
+    const bool active = (act >> (fi & 31)) & 1u;
 
     float Gx = s.gx, Gy = s.gy, Gz = s.gz;
     if (active) {  // spread force of this step; clear the buffer of the next
@@ -740,7 +759,7 @@ __device__ __forceinline__ void pair_update(const SimDev &s, int par, uint32_t f
     pair_update_act<T>(s, par, f, P, step_seed, (__ldcg(s.amask + (f >> 5)) >> (f & 31)) & 3u);
 }
 
-template <typename T>
+template <typename T, bool EARLY>
 __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uint32_t step_seed) {
     const uint16_t *__restrict__ src = (const uint16_t *)s.pop[par];
     const uint32_t nfp = (uint32_t)s.nfp, f = (uint32_t)fi;
@@ -757,6 +776,10 @@ __device__ __forceinline__ void fluid_pair(const SimDev &s, int par, int fi, uin
     LBIB_PULL2(7) LBIB_PULL2(8) LBIB_PULL2(9) LBIB_PULL2(10) LBIB_PULL2(11) LBIB_PULL2(12) LBIB_PULL2(13)
     LBIB_PULL2(14) LBIB_PULL2(15) LBIB_PULL2(16) LBIB_PULL2(17) LBIB_PULL2(18)
 #undef LBIB_PULL2
+    if constexpr (EARLY) {  // as in fluid_cell
+        dep_wait();
+        dep_release();
+    }
     pair_update<T>(s, par, f, P, step_seed);
 }
 
@@ -815,20 +838,13 @@ __host__ __device__ __forceinline__ uint32_t step_seed(long long t) {
     return x;
 }
 
-// The active-cell word of the warp that owns fluid cell f (blocks start at
-// multiples of 32, so a warp owns exactly one word).  Read through L2: the
-// object update of the same launch may set bits.
-__device__ __forceinline__ uint32_t active_word(const SimDev &s, int f) {
-    const int w = f >> 5;
-    return (w < s.nwords) ? __ldcg(s.amask + w) : 0u;
-}
 
 // One block of FLUID_THREADS consecutive fluid cells starting at f0.
-template <typename T, bool BC>
+template <typename T, bool BC, bool EARLY>
 __device__ __forceinline__ void fluid_block(const SimDev &s, int par, int f0, uint32_t step_seed) {
     const int f = f0 + (int)threadIdx.x;
-    const uint32_t act = active_word(s, f);
-    if (f < s.nf) fluid_cell<T, BC>(s, par, f, (act >> (threadIdx.x & 31)) & 1u, step_seed);
+    const uint32_t act = EARLY ? 0u : active_word(s, f);
+    if (f < s.nf) fluid_cell<T, BC, EARLY>(s, par, f, act, step_seed);
 }
 
 }  // namespace lbib

@@ -28,11 +28,12 @@ __global__ void __launch_bounds__(1024, 1) k_membrane_groups(SimDev s, int T, in
     membrane_object(s, o, ib_smem + (size_t)g * group_floats, tm);
 }
 
-// NT nodes per block (LBIB_TUNE_NODE_THREADS: 32, 64, 128 or 256)
-template <int NT>
+// NT nodes per block (LBIB_TUNE_NODE_THREADS: 32, 64, 128 or 256); EARLY:
+// the instantiation for an early (programmatic dependent) launch
+template <int NT, bool EARLY>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_nodes(SimDev s, int par) {
     const int i = blockIdx.x * NT + threadIdx.x;
-    if (i < s.nn_total) node_step(s, i, par);
+    if (i < s.nn_total) node_step<EARLY>(s, i, par);
 }
 
 cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads, int group,
@@ -69,17 +70,20 @@ cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max
     return cudaLaunchKernelEx(&cfg, k_membrane, s);
 }
 
-cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st) {
+cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st, bool pdl) {
     if (s.nn_total == 0) return cudaSuccess;
-    const int blocks = (s.nn_total + threads - 1) / threads;
-    switch (threads) {
-        case 32: k_nodes<32><<<blocks, 32, 0, st>>>(s, par); break;
-        case 64: k_nodes<64><<<blocks, 64, 0, st>>>(s, par); break;
-        case 128: k_nodes<128><<<blocks, 128, 0, st>>>(s, par); break;
-        case 256: k_nodes<256><<<blocks, 256, 0, st>>>(s, par); break;
+    const unsigned blocks = (unsigned)((s.nn_total + threads - 1) / threads);
+    switch (threads * 2 + (pdl ? 1 : 0)) {
+        case 64: return launch_dep(k_nodes<32, false>, blocks, 32, st, false, s, par);
+        case 65: return launch_dep(k_nodes<32, true>, blocks, 32, st, true, s, par);
+        case 128: return launch_dep(k_nodes<64, false>, blocks, 64, st, false, s, par);
+        case 129: return launch_dep(k_nodes<64, true>, blocks, 64, st, true, s, par);
+        case 256: return launch_dep(k_nodes<128, false>, blocks, 128, st, false, s, par);
+        case 257: return launch_dep(k_nodes<128, true>, blocks, 128, st, true, s, par);
+        case 512: return launch_dep(k_nodes<256, false>, blocks, 256, st, false, s, par);
+        case 513: return launch_dep(k_nodes<256, true>, blocks, 256, st, true, s, par);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ repulsion

@@ -310,10 +310,18 @@ __device__ __forceinline__ void triangle_force(const TplDev &T, const Stage &P, 
     F.add(tr.z, (cl * rsqrtf(dot(hc, hc))) * hc + (cg * rsqrtf(dot(wc, wc))) * wc + fv);
 }
 
-// Coupling and Newton update of node i (global index) of object o under the
-// membrane force F.
-__device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F, float inv_mass, int par) {
+// Coupling and Newton update of node i (global index) of object o.  EARLY
+// (the kernel may be launched early, by programmatic dependent launch):
+// before dep_wait() it reads only the node state and the object tables
+// (written by no kernel that can still be running when a node kernel starts
+// early); the membrane force, the external force, the velocity field, the
+// coupling buffer and the mask come after it.  Otherwise the membrane force
+// is read first.
+template <bool EARLY>
+__device__ __forceinline__ void node_update(const SimDev &s, int o, int i, float inv_mass, int par) {
     const int NN = s.nn_total;
+    f3 F;
+    if constexpr (!EARLY) F = mk(s.Fel[i], s.Fel[NN + i], s.Fel[2 * NN + i]);
     float *Xh = s.Xh, *Xl = s.Xl, *Vh = s.Vh, *Vl = s.Vl;
     df x{Xh[i], Xl[i]}, y{Xh[NN + i], Xl[NN + i]}, z{Xh[2 * NN + i], Xl[2 * NN + i]};
     if (!isfinite(x.hi) || !isfinite(y.hi) || !isfinite(z.hi)) {
@@ -326,6 +334,11 @@ __device__ __forceinline__ void node_update(const SimDev &s, int o, int i, f3 F,
     Corners c;
     corners(s, x, y, z, c);
     const int3 c0 = lower_corner(x, y, z);
+    if constexpr (EARLY) {
+        dep_wait();
+        dep_release();
+        F = mk(s.Fel[i], s.Fel[NN + i], s.Fel[2 * NN + i]);
+    }
     float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -556,11 +569,10 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
 }
 
 // Coupling part for global node i.
+template <bool EARLY>
 __device__ __forceinline__ void node_step(const SimDev &s, int i, int par) {
     const int o = s.node_obj[i];
-    const int NN = s.nn_total;
-    const f3 F = mk(s.Fel[i], s.Fel[NN + i], s.Fel[2 * NN + i]);
-    node_update(s, o, i, F, s.obj[o].inv_mass, par);
+    node_update<EARLY>(s, o, i, s.obj[o].inv_mass, par);
 }
 
 }  // namespace lbib

@@ -192,8 +192,41 @@ struct SmemAttr {
     }
 };
 
+// ---- programmatic dependent launch -------------------------------------------
+// A kernel launched with `pdl` may start while the kernel before it in the
+// stream finishes.  It reads, before dep_wait(), only data that no kernel
+// still running can be writing (see lbib_step), and after dep_wait() lets
+// the next such kernel start (dep_release()).  Without the launch attribute
+// both are no-ops.
+#if defined(__CUDACC__)
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches k<<<grid, block, 0, st>>>(args...), with programmatic stream
+// serialization when pdl.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, bool pdl, Args... args) {
+    if (!pdl) {
+        k<<<grid, block, 0, st>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+#endif
+
 // ---- launchers (fluid.cu) -------------------------------------------------
-cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st);
+// pdl: launch with programmatic stream serialization (only right after the
+// node kernel of the same step)
+cudaError_t launch_fluid(const SimDev &s, int par, long long t, cudaStream_t st, bool pdl = false);
 // the kernel launch_fluid picks (lbib_info out[7]): 0 one cell per thread,
 // 1 two cells per thread, 2 warp-specialised two cells per thread
 int fluid_kernel_kind(const SimDev &s);
@@ -222,7 +255,9 @@ cudaError_t launch_mass_partials(const SimDev &s, int pop_par, double *part, int
 // group > 1: `group` objects per block of group * threads threads instead
 cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads, int group,
                             cudaStream_t st);
-cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st);
+// pdl: launch with programmatic stream serialization (only right after the
+// previous step's fluid kernel, a mask rebuild or a membrane kernel)
+cudaError_t launch_nodes(const SimDev &s, int par, int threads, cudaStream_t st, bool pdl = false);
 // object-object repulsion added to Fel (after the membrane kernel, which
 // also writes the object bounding boxes); max_nodes sizes shared memory
 cudaError_t launch_repulsion(const SimDev &s, int max_nodes, cudaStream_t st);

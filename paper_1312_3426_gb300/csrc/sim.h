@@ -75,6 +75,7 @@ struct lbib_sim {
     int membrane_clusters = 0;          // clusters of the membrane kernel (0: one per object)
     int membrane_threads = 192;         // block size of the membrane kernel (per object)
     int membrane_group = 1;             // objects per block of the membrane kernel
+    bool early_launch = false;          // programmatic dependent launch of the node and fluid kernels
     int node_threads = lbib::IB_THREADS_DEFAULT;  // nodes per block of the node kernel
 
     double rep_obj[3] = {0, 1, 0};      // soft-sphere repulsion (a, n, cutoff) between objects

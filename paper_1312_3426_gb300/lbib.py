@@ -308,6 +308,7 @@ LBIB_TUNE_MEMBRANE_THREADS = 3
 LBIB_TUNE_FLUID_KERNEL = 4
 LBIB_TUNE_NODE_THREADS = 5
 LBIB_TUNE_MEMBRANE_GROUP = 6
+LBIB_TUNE_EARLY_LAUNCH = 7
 
 
 def lbib_set_tuning(h, key, value):

@@ -10,12 +10,15 @@ floating-point atomics, only the speed:
 * ``LBIB_TUNE_NODE_THREADS``    nodes per block of the node kernel (the node chunk);
 * ``LBIB_TUNE_FLUID_KERNEL``    16-bit storage: two cells per thread (1), the
   warp-specialised two-cells kernel (2, single simulations only) or one
-  cell per thread (3).
+  cell per thread (3);
+* ``LBIB_TUNE_EARLY_LAUNCH``    programmatic dependent launch of the node and
+  fluid kernels (single simulations).
 
 ``autotune`` times a few steps of the caller's own simulations for each
 candidate and keeps the fastest, one knob group at a time (membrane shape,
 then objects per membrane block, then the node chunk, then the fluid
-kernel, each group searched with the best choice of the groups before it).  Results are cached by a key of
+kernel, then early launch, each group searched with the best choice of the
+groups before it).  Results are cached by a key of
 the workload's shape (number of simulations, box-size class, node-count
 class, storage precisions, batched or not), so simulations of the same class
 reuse the choice.  Tuning advances the simulations it times; callers tune on
@@ -31,9 +34,10 @@ _CACHE: dict = {}
 
 KNOBS = (("cluster", lbib.LBIB_TUNE_IB_CLUSTER), ("overlap", lbib.LBIB_TUNE_OVERLAP),
          ("membrane_threads", lbib.LBIB_TUNE_MEMBRANE_THREADS), ("membrane_group", lbib.LBIB_TUNE_MEMBRANE_GROUP),
-         ("node_threads", lbib.LBIB_TUNE_NODE_THREADS), ("fluid_kernel", lbib.LBIB_TUNE_FLUID_KERNEL))
+         ("node_threads", lbib.LBIB_TUNE_NODE_THREADS), ("fluid_kernel", lbib.LBIB_TUNE_FLUID_KERNEL),
+         ("early_launch", lbib.LBIB_TUNE_EARLY_LAUNCH))
 DEFAULT = {"cluster": 1, "overlap": 1, "membrane_threads": 192, "membrane_group": 1, "node_threads": 256,
-           "fluid_kernel": 0}
+           "fluid_kernel": 0, "early_launch": 0}
 
 
 def _key(sims, batched):
@@ -84,6 +88,8 @@ def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 25
     if any(int(s.info()[6]) != lbib.LBIB_POP_F32 for s in sims):
         kernels = (1, 3) if batched else (1, 2, 3)
         groups.append((("fluid_kernel",), [(k,) for k in kernels]))
+    if not batched:  # the batched step launches plainly
+        groups.append((("early_launch",), [(0,), (1,)]))
     return groups
 
 

@@ -842,3 +842,56 @@ def test_batched_membrane_objects_per_block_equals_individual_steps(group):
             assert np.abs(xa - xm).max() <= 1e-6
         for x in alone + mixed:
             x.close()
+
+
+@pytest.mark.parametrize("prec,scale", [("f32", 0), ("f16s", 12), ("bf16s", 12)])
+@pytest.mark.parametrize("walls", [True, False])
+def test_early_launch_without_objects_stores_identical_populations(prec, scale, walls):
+    """LBIB_TUNE_EARLY_LAUNCH lets each fluid kernel of a call after the
+    first start early; the kernels compute the same values in the same order,
+    so an object-free run stores exactly the populations of plain launches,
+    step after step, across several calls."""
+    sc = scenes.Scene("rows", 38, 17, 23, walls=walls, tau=0.8, body_force=(2e-5, 1e-6, 1e-5), steps=40)
+    a = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=scale)
+    b = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=scale)
+    lbib.lbib_set_tuning(b.h, lbib.LBIB_TUNE_EARLY_LAUNCH, 1)
+    assert lbib.lbib_get_tuning(b.h, lbib.LBIB_TUNE_EARLY_LAUNCH) == 1
+    for n in (1, 7, 32):
+        a.step(n)
+        b.step(n)
+        pa, pb = a.populations(), b.populations()
+        assert np.abs(pa).max() > 0
+        assert np.array_equal(pa, pb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec,scale,bound,overlap", [("f32", 0, 1e-5, 1), ("f32", 0, 1e-5, 0),
+                                                      ("f16s", 12, 5e-3, 1)])
+def test_early_launch_with_objects_matches_oracle_and_plain(prec, scale, bound, overlap):
+    """With objects the node kernel (which starts early after the previous
+    fluid kernel, or after the membrane kernel when overlap is off) and the
+    fluid kernel after it give the oracle's result like plain launches, up to
+    the order of the FP32 spreading atomics; the active-cell mask rebuild
+    (every 128 steps) falls inside the run."""
+    sc = _two_object_scene(True, nx=37, ny=19, nz=29)
+    o = oracle.Oracle.from_scene(sc)
+    o.step(300)
+    g = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=scale)
+    h = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=scale)
+    for x in (g, h):
+        lbib.lbib_set_tuning(x.h, lbib.LBIB_TUNE_OVERLAP, overlap)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_EARLY_LAUNCH, 1)
+    for n in (1, 99, 200):
+        g.step(n)
+        h.step(n)
+    assert rel_l2(g.velocity(), o.velocity(), sc) <= bound
+    if prec == "f32":
+        assert nodes_maxabs(g, o, 2) <= NODE_BAR
+        ug, uh = g.velocity(), h.velocity()
+        assert np.abs(ug - uh).max() <= 1e-5 * np.abs(uh).max()
+        assert np.abs(g.read_nodes(-1)[0] - h.read_nodes(-1)[0]).max() <= 1e-6
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_EARLY_LAUNCH, 2)
+    g.close()
+    h.close()
