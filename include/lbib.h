@@ -398,9 +398,11 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * LBIB_TUNE_MEMBRANE_THREADS threads of a block of group x threads threads
  * (at most 1024) and the cluster knobs do not apply; the step fails with
  * LBIB_ERR_CUDA when the block does not fit (threads or shared memory).
- * lbib_batch_step takes the first simulation's, and keeps one object per
- * block when the objects' shared memory (sized for the largest) or the
- * threads do not fit.  LBIB_TUNE_EARLY_LAUNCH: 1 lets each node-update and
+ * lbib_batch_step takes the first simulation's; it runs the objects within
+ * a factor 2 of the largest in one launch and the others beside it in a
+ * second (each with shared-memory slices sized for its own largest
+ * object), with as many objects per block as fit, and keeps one object per
+ * cluster when a single size class does not fit more than one.  LBIB_TUNE_EARLY_LAUNCH: 1 lets each node-update and
  * fluid kernel of lbib_step after the first start while the kernel before
  * it finishes (programmatic dependent launch: the early part reads only data
  * that kernel does not write, and waits for it before the rest), 0 (default)

@@ -126,8 +126,14 @@ struct BatchPlan {
     int n_flp[8] = {};  // fluid items per kernel variant (see fluid_group)
     int n_fl = 0, n_nd = 0, n_mb = 0;
     int max_nodes = 0;
+    // size classes of the membrane items (largest first): the n_big items
+    // within a factor 2 of the largest, and the rest, whose largest has
+    // rest_nodes nodes (0: one class)
+    int n_big = 0, rest_nodes = 0;
     int pf_cell = 0, pf_pair = 0;  // L2 prefetch distances of the fluid launches (work items)
     cudaStream_t aux = nullptr;   // membrane kernel
+    cudaStream_t aux2 = nullptr;  // membrane kernel of the smaller size class
+    cudaEvent_t ev_rest = nullptr;
     cudaStream_t gst = nullptr;   // graph launches (the caller's stream may be the legacy one, which cannot be captured)
     cudaEvent_t ev_nodes = nullptr, ev_membrane = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -190,6 +196,8 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
         int lo = 0, hi = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g_plan.aux, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g_plan.aux2, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_rest, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g_plan.gst, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_plan.ev_nodes, cudaEventDisableTiming);
@@ -252,6 +260,10 @@ static cudaError_t build_plan(lbib_sim *const *sims, int n, int cluster, cudaStr
         g_plan.pf_pair = sms;          // 1 block per SM ahead (3 resident)
     }
     g_plan.max_nodes = max_nodes;
+    g_plan.n_big = 0;
+    while (g_plan.n_big < (int)mb.size() && 2 * sims[mb[g_plan.n_big].x]->objs[mb[g_plan.n_big].y].nn > max_nodes)
+        ++g_plan.n_big;
+    g_plan.rest_nodes = g_plan.n_big < (int)mb.size() ? sims[mb[g_plan.n_big].x]->objs[mb[g_plan.n_big].y].nn : 0;
     return g_plan.n_mb ? set_membrane_attrs(ib_smem_bytes(max_nodes)) : cudaSuccess;
 }
 
@@ -264,21 +276,44 @@ static cudaError_t launch_repulsion_batch(cudaStream_t st) {
     return cudaSuccess;
 }
 
+// Membrane items [first, first + n) with up to G per block, each with a
+// shared-memory slice for max_nodes nodes (G drops to what fits).
+static cudaError_t launch_membrane_groups(cudaStream_t st, int first, int n, int max_nodes, int G) {
+    const size_t per = ib_smem_bytes(max_nodes);
+    while (G > 1 && (G * g_plan.mthreads > 1024 || per * G > (size_t)227 * 1024)) --G;
+    static SmemAttr gattr;
+    cudaError_t e = gattr.ensure((const void *)k_batch_membrane_groups, per * G, false);
+    if (e != cudaSuccess) return e;
+    const int blocks = (n + G - 1) / G;
+    k_batch_membrane_groups<<<blocks, G * g_plan.mthreads, per * G, st>>>(
+        (const SimDev *)g_plan.d_sims, (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd + first), n,
+        g_plan.mthreads, (int)(per / sizeof(float)));
+    return cudaGetLastError();
+}
+
+// On `st` (which waits for the node update): the membrane forces, then the
+// repulsion.  With several objects per block, the objects within a factor 2
+// of the largest run in one launch (their slices sized for the largest) and
+// the others beside it on a second stream (slices sized for theirs), so a
+// level-2 object does not hold the shared memory of a level-4 one.
 static cudaError_t launch_membrane_batch(cudaStream_t st) {
     if (g_plan.n_mb == 0) return cudaSuccess;
-    const size_t per = ib_smem_bytes(g_plan.max_nodes);
     const int G = g_plan.mgroup;
-    if (G > 1 && G * g_plan.mthreads <= 1024 && per * G <= (size_t)227 * 1024) {
-        // several objects per block (the shared-memory slice of each is sized for the largest object)
-        static SmemAttr gattr;
-        cudaError_t e = gattr.ensure((const void *)k_batch_membrane_groups, per * G, false);
-        if (e != cudaSuccess) return e;
-        const int blocks = (g_plan.n_mb + G - 1) / G;
-        k_batch_membrane_groups<<<blocks, G * g_plan.mthreads, per * G, st>>>(
-            (const SimDev *)g_plan.d_sims, (const int2 *)(g_plan.d_items + g_plan.n_fl + g_plan.n_nd), g_plan.n_mb,
-            g_plan.mthreads, (int)(per / sizeof(float)));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t per = ib_smem_bytes(g_plan.max_nodes);
+    if (G > 1 && g_plan.n_big < g_plan.n_mb) {
+        cudaError_t e;
+        if ((e = cudaStreamWaitEvent(g_plan.aux2, g_plan.ev_nodes, 0)) != cudaSuccess) return e;
+        if ((e = launch_membrane_groups(g_plan.aux2, g_plan.n_big, g_plan.n_mb - g_plan.n_big, g_plan.rest_nodes, G)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(g_plan.ev_rest, g_plan.aux2)) != cudaSuccess) return e;
+        if ((e = launch_membrane_groups(st, 0, g_plan.n_big, g_plan.max_nodes, G)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, g_plan.ev_rest, 0)) != cudaSuccess) return e;
         return launch_repulsion_batch(st);
+    }
+    if (G > 1 && G * g_plan.mthreads <= 1024 && per * G <= (size_t)227 * 1024) {
+        cudaError_t e = launch_membrane_groups(st, 0, g_plan.n_mb, g_plan.max_nodes, G);
+        return e == cudaSuccess ? launch_repulsion_batch(st) : e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(g_plan.n_mb * g_plan.cluster));

@@ -75,7 +75,7 @@ def apply(sims, choice):
             lbib.lbib_set_tuning(s.h, key, int(choice[name]))
 
 
-def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), member_groups=(1, 2, 3),
+def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), member_groups=(1, 2, 3, 4),
                node_threads=(64, 128, 256)):
     """The knob groups searched, in order: [(name, ...), [values, ...]]."""
     groups = []
