@@ -15,10 +15,10 @@ floating-point atomics, only the speed:
   fluid kernels (single simulations).
 
 ``autotune`` times a few steps of the caller's own simulations for each
-candidate and keeps the fastest, one knob group at a time (membrane shape,
-then objects per membrane block, then the node chunk, then the fluid
-kernel, then early launch, each group searched with the best choice of the
-groups before it).  Results are cached by a key of
+candidate and keeps the fastest, one knob group at a time (membrane
+clusters and overlap, then threads per object together with objects per
+membrane block, then the node chunk, then the fluid kernel, then early
+launch, each group searched with the best choice of the groups before it).  Results are cached by a key of
 the workload's shape (number of simulations, box-size class, node-count
 class, storage precisions, batched or not), so simulations of the same class
 reuse the choice.  Tuning advances the simulations it times; callers tune on
@@ -75,15 +75,19 @@ def apply(sims, choice):
             lbib.lbib_set_tuning(s.h, key, int(choice[name]))
 
 
-def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(192, 256), member_groups=(1, 2, 3, 4),
-               node_threads=(64, 128, 256)):
-    """The knob groups searched, in order: [(name, ...), [values, ...]]."""
+def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(128, 192, 256),
+               member_groups=(1, 2, 3, 4, 5, 6), node_threads=(64, 128, 256)):
+    """The knob groups searched, in order: [(name, ...), [values, ...]].
+    Threads per object and objects per block are searched together: fewer
+    threads leave more of each SM to the fluid kernel beside the membrane
+    kernel until the membrane kernel becomes the longer of the two, and
+    where that happens depends on how many objects share a block."""
     groups = []
     has_objects = any(int(s.info()[1]) > 0 for s in sims)
     if has_objects:
-        groups.append((("cluster", "overlap", "membrane_threads"),
-                       [(c, o, t) for c in clusters for o in overlaps for t in threads]))
-        groups.append((("membrane_group",), [(g,) for g in member_groups]))
+        groups.append((("cluster", "overlap"), [(c, o) for c in clusters for o in overlaps]))
+        groups.append((("membrane_threads", "membrane_group"),
+                       [(t, g) for t in threads for g in member_groups if t * g <= 1024]))
         groups.append((("node_threads",), [(t,) for t in node_threads]))
     if any(int(s.info()[6]) != lbib.LBIB_POP_F32 for s in sims):
         kernels = (1, 3) if batched else (1, 2, 3)
