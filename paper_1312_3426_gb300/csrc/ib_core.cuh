@@ -237,7 +237,9 @@ struct Forces {
 // they share the record, the staged positions of b and c and the vector
 // c - b, and their forces on b and c are summed before the shared-memory
 // reductions (the order of FP32 additions into a node is not fixed anyway).
-__device__ __forceinline__ void hinge_force(const TplDev &T, const Stage &P, int e, const Forces &F) {
+template <bool AV>
+__device__ __forceinline__ void hinge_force(const TplDev &T, const Stage &P, int e, const Forces &F, df &area,
+                                            df &vol) {
     const int4 q = __ldg(T.quad + e);
     const float4 h = __ldg(T.hinge + e);  // (L0, 1/L0, 1/theta0, 0)
     const f3 C = P.rel(q.z, q.y);         // c - b
@@ -259,6 +261,10 @@ __device__ __forceinline__ void hinge_force(const TplDev &T, const Stage &P, int
         const f3 A = P.rel(q.x, q.y), D = P.rel(q.w, q.y);  // relative to b
         f3 n1 = cross(-1.f * A, C - A);  // (b-a) x (c-a)
         f3 n2 = cross(C - D, -1.f * D);  // (c-d) x (b-d)
+        if constexpr (AV) {  // each triangle is in three hinges: a third of its area and volume term each
+            area = df_add_f(area, 0.5f * (sqrtf(dot(n1, n1)) + sqrtf(dot(n2, n2))));
+            vol = df_add_f(vol, dot(P.pos(q.x), n1) + dot(P.pos(q.w), n2));
+        }
         n1 = rsqrtf(dot(n1, n1)) * n1;
         n2 = rsqrtf(dot(n2, n2)) * n2;
         const f3 cr = cross(n1, n2);
@@ -494,9 +500,22 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
     // 1b. bounding box of the object's nodes (broad phase of the repulsion)
     if (s.rep_on && r == 0) object_box(s, o, P, nn, f0, tail, tm);
 
-    // 2. this block's share of the area and volume sums
+    // 2. this block's share of the area and volume sums: with bending on,
+    //    from the hinge pass (each triangle three times), else by triangle
     df area{0.f, 0.f}, vol{0.f, 0.f};
-    if (T.kag != 0.f || T.kv != 0.f) {
+    const bool need_av = T.kag != 0.f || T.kv != 0.f;
+    const bool av_in_hinges = need_av && T.kb != 0.f;
+    if (T.ks != 0.f || T.kb != 0.f) {
+        const int e1 = share_lo32(T.ne, r + 1, C);
+        if (av_in_hinges) {
+#pragma unroll 2
+            for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) hinge_force<true>(T, P, e, F, area, vol);
+        } else {
+#pragma unroll 2
+            for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) hinge_force<false>(T, P, e, F, area, vol);
+        }
+    }
+    if (need_av && !av_in_hinges) {
         for (int t = share_lo(T.nt, r, C) + tid; t < share_lo(T.nt, r + 1, C); t += nthr) {
             const int4 tr = __ldg(T.tri + t);
             const f3 N = cross(P.rel(tr.y, tr.x), P.rel(tr.z, tr.x));
@@ -529,6 +548,10 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
             Sg += (double)pj[0] + (double)pj[1];
             V6 += (double)pj[2] + (double)pj[3];
         }
+        if (av_in_hinges) {  // every triangle was summed three times
+            Sg *= 1.0 / 3.0;
+            V6 *= 1.0 / 3.0;
+        }
         // differences to the relaxed state in FP64, ratios in FP32
         const float dS = (float)(Sg - T.Sg0), dVol = (float)(V6 * (-1.0 / 6.0) - T.V0);
         tail[4] = (T.kag != 0.f) ? dS / (float)Sg : 0.f;
@@ -539,11 +562,6 @@ __device__ __forceinline__ void membrane_object(const SimDev &s, int o, float *s
 
     // 3. this block's share of each kind of element; one loop per kind so
     //    that independent iterations overlap
-    if (T.ks != 0.f || T.kb != 0.f) {
-        const int e1 = share_lo32(T.ne, r + 1, C);
-#pragma unroll 2
-        for (int e = share_lo32(T.ne, r, C) + tid; e < e1; e += nthr) hinge_force(T, P, e, F);
-    }
     if (T.kal != 0.f || T.kag != 0.f || T.kv != 0.f) {
         const int t1 = share_lo32(T.nt, r + 1, C);
 #pragma unroll 2
