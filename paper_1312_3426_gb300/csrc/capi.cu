@@ -51,8 +51,10 @@ bool fluid_layout(const lbib_fluid_params &p, FluidLayout &L) {
     return true;
 }
 
+// device records of a template: triangles (int4), and per edge its hinge
+// nodes (int4) and constants (float4)
 size_t template_bytes(const Topology &T) {
-    return align_up((size_t)T.nt * 16, 256) + 2 * align_up((size_t)T.ne * 16, 256) + align_up((size_t)T.ne * 4, 256);
+    return align_up((size_t)T.nt * 16, 256) + 2 * align_up((size_t)T.ne * 16, 256);
 }
 
 lbib_status fail(lbib_sim *s, lbib_status code, const std::string &msg) {
