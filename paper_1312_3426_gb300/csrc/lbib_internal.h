@@ -71,13 +71,13 @@ enum : uint32_t {
     ST_PAIRS = 8u,        // more close object pairs than the repulsion pair list holds
 };
 
-// Element lists of one template (device), all node ids local to an object:
+// Element lists of one template (device), all node ids local to an object,
+// each in the bank-aware evaluation order of topology.cpp:
 //   tri:        (a, b, c, rest area S0 as float bits), inward-ordered as given
-//   edge:       (a, b, rest length L0, 1/L0 as float bits), a < b,
-//               lexicographic
-//   quad:       (a, b, c, d) for edge (b, c): (a,b,c) and (d,c,b) are the
-//               inward cyclic orders of the two triangles sharing it;
-//               inv_theta0: 1 / its rest inner angle
+//   quad:       per edge (b, c), b < c: (a, b, c, d), where (a,b,c) and
+//               (d,c,b) are the inward cyclic orders of the two triangles
+//               sharing it
+//   hinge:      per edge, (rest length L0, 1/L0, 1/rest inner angle, 0)
 struct TplDev {
     int nn, nt, ne;
     float ks, kb, kal, kag, kv;
@@ -85,8 +85,6 @@ struct TplDev {
     int kal_altitude;  // local-area force along the altitudes (else centroid -> vertex)
     double Sg0, V0;
     const int4 *tri;
-    // per edge (b, c) with its two triangles (a, b, c) and (d, c, b): the
-    // nodes (a, b, c, d) and (L0, 1/L0, 1/theta0, 0), in one order
     const int4 *quad;
     const float4 *hinge;
 };
