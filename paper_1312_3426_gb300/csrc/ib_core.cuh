@@ -103,12 +103,6 @@ struct Stage {
     }
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 struct Corners {
     int f[8];
     float w[8];
