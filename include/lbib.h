@@ -296,6 +296,16 @@ LBIB_API lbib_status lbib_objects_analyze_wait(lbib_sim *sim, int slot, double *
 LBIB_API lbib_status lbib_profile_enable(lbib_sim *sim, int on);
 LBIB_API lbib_status lbib_profile_read(lbib_sim *sim, double out[6]);
 
+/* Check of the device-side bounded waits (the warp-specialised fluid
+ * kernel's pipeline waits give up after about 2 s, set the status the next
+ * call reports as LBIB_ERR_TIMEOUT, and leave the context usable instead
+ * of hanging).  Runs one such wait on the current device, on a barrier that
+ * nothing completes (arrive = 0) or that its own thread completes first
+ * (arrive = 1), bounded by `seconds`; *timed_out = 1 when the wait gave up.
+ * Returns after the wait.  LBIB_ERR_ARG for a null output or seconds outside
+ * (0, 10]; LBIB_ERR_CUDA when the device calls fail. */
+LBIB_API lbib_status lbib_check_bounded_wait(double seconds, int arrive, int *timed_out);
+
 /* Total fluid mass sum_cells sum_i f_i, an FP64 reduction on the GPU. */
 LBIB_API lbib_status lbib_fluid_mass(lbib_sim *sim, double *mass);
 

@@ -1026,6 +1026,23 @@ lbib_status lbib_fluid_mass(lbib_sim *s, double *mass) {
 // cudaMalloc / cudaMallocAsync / cudaFree and no pinned host buffer; the
 // partials live in the library's static device scratch and come back into
 // a stack array.
+lbib_status lbib_check_bounded_wait(double seconds, int arrive, int *timed_out) {
+    if (!timed_out || !(seconds > 0.0) || seconds > 10.0) return LBIB_ERR_ARG;
+    uint32_t *d = nullptr, h = 0;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = run_wait_probe(d, (unsigned long long)(seconds * 1e9), arrive ? 1 : 0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d) cudaFree(d);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return LBIB_ERR_CUDA;
+    *timed_out = (h & ST_TIMEOUT) ? 1 : 0;
+    return LBIB_OK;
+}
+
 lbib_status lbib_fluid_mass_noalloc(lbib_sim *s, double *mass) {
     LBIB_GUARD(s);  // makes the simulation's device current
     if (!mass) return fail(s, LBIB_ERR_ARG, "null output");

@@ -74,14 +74,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Waits until the phase with the given parity of *bar has completed; false
-// when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// when the bound (ns of the global timer) ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t bound_ns = TMA_WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > TMA_WAIT_NS) return false;
+        if ((i & 255u) == 255u && global_ns() - t0 > bound_ns) return false;
     }
+}
+
+// Check of the bounded wait itself: one thread waits on a barrier that
+// nothing arrives at; when the bound runs out it sets ST_TIMEOUT in *status
+// and returns, and the context stays usable.  arrive != 0: the thread
+// arrives first, so the wait completes at once (the control case).
+__global__ void k_wait_probe(uint32_t *status, unsigned long long bound_ns, int arrive) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0, bound_ns)) atomicOr(status, ST_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+}
+
+cudaError_t run_wait_probe(uint32_t *status, unsigned long long bound_ns, int arrive, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(status, bound_ns, arrive);
+    return cudaGetLastError();
 }
 
 // One bulk copy of `bytes` (a multiple of 16) from global to this block's

@@ -231,6 +231,8 @@ int fluid_kernel_kind(const SimDev &s);
 // fluid_tma.cu: the warp-specialised kernel and whether the shape allows it
 bool fluid_tma_shape(const SimDev &s);
 cudaError_t launch_fluid_tma(const SimDev &s, int par, uint32_t seed, cudaStream_t st);
+// the bounded-wait check of fluid_tma.cu (lbib_check_bounded_wait)
+cudaError_t run_wait_probe(uint32_t *status, unsigned long long bound_ns, int arrive, cudaStream_t st);
 cudaError_t launch_fields(const SimDev &s, int pop_par, int gmode, float *u_full, float *rho_full, int to_ufield,
                           cudaStream_t st);
 cudaError_t launch_read_coupling(const SimDev &s, int gpar, float *g_full, cudaStream_t st);

@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "lbib_get_tuning": (st, [P, C.c_int, C.POINTER(C.c_int)]),
         "lbib_profile_read": (st, [P, P]),
         "lbib_abi_version": (C.c_int, []),
+        "lbib_check_bounded_wait": (st, [C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "lbib_server_create": (st, [C.c_int64, C.c_int, C.c_int, C.POINTER(P)]),
         "lbib_server_destroy": (None, [P]),
         "lbib_server_admit": (st, [P, P, C.c_int64, C.c_int64]),
@@ -420,6 +421,16 @@ def lbib_batch_step(handles, n_steps=1):
 
 def lbib_abi_version():
     return int(load().lbib_abi_version())
+
+
+def lbib_check_bounded_wait(seconds, arrive=False):
+    """True when a device wait on a barrier bounded by `seconds` gave up."""
+    load()
+    out = C.c_int(-1)
+    st = _lib.lbib_check_bounded_wait(float(seconds), int(bool(arrive)), C.byref(out))
+    if st != LBIB_OK:
+        raise LbibError(st, "")
+    return bool(out.value)
 
 
 def lbib_server_create(budget_bytes, max_resident, chunk_steps):

@@ -115,6 +115,14 @@ def test_server_host_logic_without_gpu():
         lbib.lbib_server_destroy(srv)
 
 
+def test_bounded_wait_check_argument_errors_without_gpu():
+    """The wait check rejects a bound outside (0, 10] s before any device call."""
+    for sec in (0.0, -1.0, 11.0, float("nan")):
+        with pytest.raises(lbib.LbibError) as e:
+            lbib.lbib_check_bounded_wait(sec)
+        assert e.value.status == lbib.LBIB_ERR_ARG
+
+
 def test_mesh_orientation_check_repair_flip():
     """Sec. 5 mesh analysis: a consistently inward mesh needs no change;
     flipping every triangle is undone by the repair; a random subset of
