@@ -7,6 +7,9 @@ on every 16th step), against the FP64 oracle run from the same scene.  Every
 fluid cell and every node is compared after 200 steps, across one rebuild of
 the active-cell mask (every 128 steps).
 
+The 512x256x256 channel with 2000 cells (1,284,000 nodes, 33.3 M fluid
+cells) runs 32 steps the same way, in the shapes the benchmark picks there.
+
 The batch of 64 independent channels (boxes 32^3..128x64x64, 0-40 cells of
 levels 2-4, 618,048 nodes) runs as the benchmark runs it: one batched call,
 graph-captured 16-step chunks, two size classes of membrane launches of four
@@ -93,6 +96,51 @@ def test_rbc_channel_256x128x128_200_steps_matches_oracle(reference, prec):
     else:
         assert err_u <= 1e-3, err_u
         assert err_x <= STEPS * 1e-3 * umax, err_x
+
+
+LARGE_STEPS = 32
+LARGE_SHAPES = {
+    "f32": dict(SHAPES["f32"], membrane_group=2, early_launch=0),
+    "f16s": dict(SHAPES["f16s"], membrane_group=4),
+}
+
+
+@pytest.fixture(scope="module")
+def reference_large():
+    sc = scenes.channel_rbc_large()
+    o = oracle.Oracle.from_scene(sc)
+    n = len(sc.objects)
+    x0 = [o.read_nodes(i)[0] for i in range(n)]
+    o.step(LARGE_STEPS)
+    u = o.velocity()
+    x = [o.read_nodes(i)[0] for i in range(n)]
+    del o
+    moved = max(float(np.abs(a - b).max()) for a, b in zip(x, x0))
+    return sc, u, x, moved
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_rbc_channel_512x256x256_32_steps_matches_oracle(reference_large, prec):
+    sc, uo, xo, moved = reference_large
+    g = lbib.Sim.from_scene(sc, precision=prec, pop_scale_log2=0 if prec == "f32" else 12)
+    tune.apply([g], LARGE_SHAPES[prec])
+    lbib.lbib_profile_enable(g.h, 4)
+    g.step(LARGE_STEPS)
+    g.sync()
+    xg = [g.read_nodes(i)[0] for i in range(len(sc.objects))]
+    ug = g.velocity()
+    g.close()
+    err_u, err_x = errors(sc, ug, xg, uo, xo)
+    umax = float(np.sqrt((uo ** 2).sum(0)).max())
+    print(f"\n512x256x256, 2000 RBCs, {LARGE_STEPS} steps, {prec}: velocity rel L2 {err_u:.3e}, node max-abs "
+          f"{err_x:.3e} lu (nodes moved up to {moved:.3e} lu, u_max {umax:.3e})")
+    assert moved > 1e-4
+    if prec == "f32":
+        assert err_u <= 1e-5, err_u
+        assert err_x <= 1e-6, err_x
+    else:
+        assert err_u <= 1e-3, err_u
+        assert err_x <= LARGE_STEPS * 1e-3 * umax, err_x
 
 
 BATCH_STEPS = 144
