@@ -159,3 +159,22 @@ def test_vtk_roundtrip(tmp_path):
     vtk.write_vtk(p, nodes * 8.0, tris, {"speed": np.arange(len(nodes), dtype=float)})
     X, T = vtk.read_vtk(p)
     assert np.array_equal(X, nodes * 8.0) and np.array_equal(T, tris)
+
+
+# The largest box: population indices are 32-bit (19 x padded cells < 2^32).
+MAX_BOX = (1024, 217, 1024)  # walls in y: 215 fluid rows, 225,443,840 fluid cells
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16s"])
+def test_largest_box_accepted_one_row_more_refused(prec):
+    nx, ny, nz = MAX_BOX
+    nf = nx * (ny - 2) * nz
+    assert 19 * nf < 2 ** 32 <= 19 * nx * (ny - 1) * nz
+    esz = 4 if prec == "f32" else 2
+    ok = lbib.lbib_footprint_bytes(lbib.fluid_params(nx, ny, nz, precision=prec), 0, 0)
+    assert ok >= 2 * 19 * esz * nf + 3 * 16 * nf
+    too_big = lbib.fluid_params(nx, ny + 1, nz, precision=prec)
+    assert lbib.lbib_footprint_bytes(too_big, 0, 0) == -1
+    with pytest.raises(lbib.LbibError) as e:  # refused before any device call
+        lbib.lbib_create(too_big)
+    assert e.value.status == lbib.LBIB_ERR_ARG
