@@ -406,8 +406,9 @@ LBIB_API lbib_status lbib_server_stats(const lbib_server *srv, int64_t out[4]);
  * simulation's).  LBIB_TUNE_MEMBRANE_GROUP: objects per block of the
  * membrane-force kernel (1..15, default 1); above 1 each object gets
  * LBIB_TUNE_MEMBRANE_THREADS threads of a block of group x threads threads
- * (at most 1024) and the cluster knobs do not apply; the step fails with
- * LBIB_ERR_CUDA when the block does not fit (threads or shared memory).
+ * (at most 1024) and the cluster knobs do not apply; the step takes as
+ * many objects per block as fit (threads and shared memory for the largest
+ * template), at most the knob's value.
  * lbib_batch_step takes the first simulation's; it runs the objects within
  * a factor 2 of the largest in one launch and the others beside it in a
  * second (each with shared-memory slices sized for its own largest

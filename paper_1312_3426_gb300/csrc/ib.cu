@@ -39,10 +39,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_nodes(SimDev s, int par) {
 cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max_clusters, int threads, int group,
                             cudaStream_t st) {
     if (s.nobj == 0) return cudaSuccess;
+    // as many objects per block as fit (threads and shared memory), at most `group`
+    const size_t per = ib_smem_bytes(max_nodes);  // a multiple of 16 bytes
+    while (group > 1 && (group * threads > 1024 || group > 15 || per * (size_t)group > 227 * 1024)) --group;
     if (group > 1) {  // several objects per block (cluster size and cluster count do not apply)
-        const size_t per = ib_smem_bytes(max_nodes);  // a multiple of 16 bytes
         const size_t smem = per * (size_t)group;
-        if (group * threads > 1024 || group > 15 || smem > 227 * 1024) return cudaErrorInvalidValue;
         static SmemAttr gattr;
         cudaError_t eg = gattr.ensure((const void *)k_membrane_groups, smem, false);
         if (eg != cudaSuccess) return eg;
@@ -50,7 +51,7 @@ cudaError_t launch_membrane(const SimDev &s, int max_nodes, int cluster, int max
         k_membrane_groups<<<blocks, group * threads, smem, st>>>(s, threads, (int)(per / sizeof(float)));
         return cudaGetLastError();
     }
-    const size_t smem = ib_smem_bytes(max_nodes);
+    const size_t smem = per;
     static SmemAttr attr;
     cudaError_t ea = attr.ensure((const void *)k_membrane, smem, true);
     if (ea != cudaSuccess) return ea;

@@ -3,7 +3,7 @@ are deterministic and have the sizes, spacings and counts the design notes
 quote.  Inputs only: none of the method's arithmetic is here."""
 import numpy as np
 
-from workloads import scenes
+from workloads import mesh, scenes
 
 
 def _min_image_separation(sc):
@@ -70,3 +70,28 @@ def test_serving_trace_recipe():
     again = scenes.serving_trace(32, seed=4, rate_per_s=10.0)
     key = lambda r: (r.arrival_s, r.steps, r.scene.nx)  # noqa: E731
     assert [key(r) for r in again] == [key(r) for r in reqs[:32]]
+
+
+def test_octasphere_counts_closed_and_inward():
+    """4 * 4^L + 2 nodes and 8 * 4^L triangles on the unit sphere; every edge
+    shared by exactly two triangles (V - E + F = 2); inward orientation
+    (negative signed volume sum A . (B x C) for the inward reading); the
+    enclosed volume rises from the octahedron's 4/3 towards the sphere's."""
+    prev = 0.0
+    for level in range(4):
+        nodes, tris = mesh.octasphere(level)
+        assert len(nodes) == 4 * 4 ** level + 2 and len(tris) == 8 * 4 ** level
+        assert np.allclose(np.linalg.norm(nodes, axis=1), 1.0)
+        edges = {}
+        for a, b, c in tris:
+            for i, j in ((a, b), (b, c), (c, a)):
+                edges[(min(i, j), max(i, j))] = edges.get((min(i, j), max(i, j)), 0) + 1
+        assert set(edges.values()) == {2}
+        assert len(nodes) - len(edges) + len(tris) == 2
+        a, b, c = nodes[tris[:, 0]], nodes[tris[:, 1]], nodes[tris[:, 2]]
+        v6 = float(np.einsum("ij,ij->i", a, np.cross(b, c)).sum())
+        assert v6 < 0.0
+        vol = -v6 / 6.0  # the regular octahedron of unit circumradius has volume 4/3
+        assert (abs(vol - 4.0 / 3.0) < 1e-12) if level == 0 else (prev < vol < 4.0 / 3.0 * np.pi)
+        prev = vol
+    assert vol > 0.97 * 4.0 / 3.0 * np.pi

@@ -135,3 +135,35 @@ def octahedron() -> tuple[np.ndarray, np.ndarray]:
     f = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4],
                   [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]], dtype=np.int64)
     return v, _orient_inward(v, f).astype(np.int32)
+
+
+def octasphere(level: int) -> tuple[np.ndarray, np.ndarray]:
+    """Unit sphere from the octahedron by `level` midpoint subdivisions
+    (4 * 4^level + 2 nodes, 8 * 4^level triangles; level 5: 4098 nodes,
+    near the largest template the library stages), inward-oriented."""
+    if level < 0:
+        raise ValueError("level must be >= 0")
+    v, f = octahedron()
+    verts = [tuple(p) for p in v]
+    faces = [tuple(int(i) for i in t) for t in f]
+    for _ in range(level):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(i: int, j: int) -> int:
+            key = (i, j) if i < j else (j, i)
+            k = cache.get(key)
+            if k is None:
+                p = np.add(verts[i], verts[j]) * 0.5
+                verts.append(tuple(p / np.linalg.norm(p)))
+                k = len(verts) - 1
+                cache[key] = k
+            return k
+
+        new = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = new
+    nodes = np.array(verts, dtype=np.float64)
+    tris = _orient_inward(nodes, np.asarray(faces, dtype=np.int64))
+    return nodes, tris.astype(np.int32)
