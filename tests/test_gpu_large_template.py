@@ -69,3 +69,61 @@ def test_largest_template_matches_oracle(reference, cluster, group):
     assert moved > 0.05
     assert err_u <= 1e-5, err_u
     assert err_x <= 1e-6, err_x
+
+
+@pytest.mark.parametrize("cluster,group", [(1, 1), (2, 1), (1, 3)])
+def test_smallest_templates_match_oracle(cluster, group):
+    """The smallest closed meshes: a tetrahedron (4 nodes, 6 edges: fewer
+    elements than a warp) and an icosahedron (12 nodes), deformed, beside
+    each other in the channel, 300 steps.  Node mass 10: with triangles this
+    large the volume and area forces are stiff enough that the explicit
+    update of unit-mass nodes diverges (in the oracle too)."""
+    sc = scenes.Scene("tet_ico_40x24x40", 40, 24, 40, steps=STEPS)
+    for m, r in ((mesh.tetrahedron(), 2.0), (mesh.icosphere(0), 3.0)):
+        sc.templates.append(scenes.Template(m[0], m[1], (r, r, r), **scenes.PAPER_MODULI))
+    sc.objects += [scenes.Obj(0, (12.0, 12.0, 20.0), mass=10.0), scenes.Obj(1, (28.0, 12.0, 20.0), mass=10.0)]
+    o = oracle.Oracle.from_scene(sc)
+    g = lbib.Sim.from_scene(sc)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_IB_CLUSTER, cluster)
+    lbib.lbib_set_tuning(g.h, lbib.LBIB_TUNE_MEMBRANE_GROUP, group)
+    start = []
+    for oid in range(2):
+        X, _ = o.read_nodes(oid)
+        c = X.mean(0)
+        Xd = c + (X - c) * np.array([1.1, 1.0 / 1.1, 1.0])
+        o.object_set_nodes(oid, Xd)
+        g.object_set_nodes(oid, Xd)
+        start.append(Xd)
+    o.step(STEPS)
+    g.step(STEPS)
+    g.sync()
+    rows = slice(1, sc.ny - 1)
+    ug, uo = g.velocity(), o.velocity()
+    err_u = float(np.linalg.norm(ug[:, :, rows, :].astype(np.float64) - uo[:, :, rows, :]) /
+                  np.linalg.norm(uo[:, :, rows, :]))
+    err_x = max(float(np.abs(g.read_nodes(i)[0] - o.read_nodes(i)[0]).max()) for i in range(2))
+    moved = min(float(np.abs(o.read_nodes(i)[0] - start[i]).max()) for i in range(2))
+    g.close()
+    print(f"\ntetrahedron + icosahedron, cluster {cluster}, group {group}: velocity rel L2 {err_u:.3e}, "
+          f"node max-abs {err_x:.3e} lu")
+    assert moved > 0.01
+    assert err_u <= 1e-5, err_u
+    assert err_x <= 1e-6, err_x
+
+
+def test_autotune_single_simulation_with_level4_objects():
+    """The autotuner's objects-per-block candidates exceed what fits for a
+    level-4 object (113 KB each): the launch takes what fits, so every
+    candidate runs and the simulation stays usable."""
+    from paper_1312_3426_gb300 import tune
+    sc = scenes.Scene("rbc_l4_48x28x48", 48, 28, 48, steps=64)
+    nodes, tris = mesh.biconcave(4)
+    sc.templates.append(scenes.Template(nodes, tris, (8.0, 8.0, 8.0), **scenes.PAPER_MODULI))
+    sc.objects += [scenes.Obj(0, (14.0, 14.0, 24.0)), scenes.Obj(0, (34.0, 14.0, 24.0))]
+    g = lbib.Sim.from_scene(sc)
+    choice, timing = tune.autotune([g], steps=8, batched=False)
+    assert any(k.endswith("membrane_group=6") for k in timing)
+    g.step(8)
+    g.sync()
+    assert np.isfinite(g.velocity()).all()
+    g.close()
