@@ -75,7 +75,7 @@ def apply(sims, choice):
             lbib.lbib_set_tuning(s.h, key, int(choice[name]))
 
 
-def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(128, 192, 256),
+def candidates(sims, batched, clusters=(1, 2), overlaps=(1, 0), threads=(96, 128, 192, 256),
                member_groups=(1, 2, 3, 4, 5, 6), node_threads=(64, 128, 256)):
     """The knob groups searched, in order: [(name, ...), [values, ...]].
     Threads per object and objects per block are searched together: fewer
